@@ -1,0 +1,316 @@
+#!/usr/bin/env python
+"""Throughput of high-precision SSPPR queries (l1 <= 1e-8) on one GB300.
+
+Workload (default ``rmat20-k64``): R-MAT scale 20, edge factor 16,
+(a, b, c, d) = (0.57, 0.19, 0.19, 0.05), duplicates and self-loops removed,
+sinks patched; alpha = 0.2, lambda = 1e-8; one step = one batch of 64 uniform
+random sources (seed 2) answered by one ``ppr_sssp_query`` call.  Synthetic
+data: the graph stands in for the paper's SNAP graphs.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle
+(Algorithm 3 run single-threaded, as the paper's C++ did) on the same graph
+and sources, one query per step.
+
+Multi-GPU: queries are independent, so N processes (torchrun) each answer
+their own batches (replicas, no collective on the data path); the timed
+region is bracketed by barriers and the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (scale, edge_factor, k per step, k_tile)
+    "rmat20-k64": (20, 16, 64, 8),
+    "rmat20-k8": (20, 16, 8, 8),
+    "rmat22-k1": (22, 16, 1, 1),
+}
+ALPHA, LAMBDA = 0.2, 1e-8
+METRIC = "SSPPR queries/s at l1<=1e-8 (HP, plain GPU method)"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def sweep_bytes(n: int, m: int, kt: int) -> int:
+    """Algorithmic DRAM bytes of one sweep launch over a tile of kt sources:
+    in-CSR (row_ptr 4(n+1), col_idx 4m), per-node scales (8 + 4 per node) and
+    the tile's z vector read once and written once (2 * 8 kt per node)."""
+    return 4 * (n + 1) + 4 * m + 12 * n + 16 * n * kt
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for name in ("hp.cu", "ppr_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2101_03652_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str):
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "sweep_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        if rec.get("kernel_source_sha") == kernel_source_sha() and rec.get("workload") == workload:
+            return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_inputs(workload: str, rank: int):
+    import ppr_inputs as gen
+    scale, ef, k, kt = WORKLOADS[workload]
+    rp, ci = gen.rmat(scale, ef, seed=1)
+    src = gen.sources(len(rp) - 1, k, seed=2 + 1000 * rank)
+    return rp, ci, src, kt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    rp, ci, src, _ = make_inputs(args.workload, 0)
+    g = O.Graph(rp, ci)
+    oracle_lam = LAMBDA
+    times = []
+    for i in range(args.warmup + args.steps):
+        s = int(src[i % len(src)])
+        t = time.perf_counter()
+        O.powerpush(g, s, ALPHA, oracle_lam)
+        dt = time.perf_counter() - t
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = args.steps / total
+    sample = f"{args.steps} sources of the workload, one Algorithm 3 query per step, FP64, single thread"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "graph": f"R-MAT scale {WORKLOADS[args.workload][0]}",
+                   "n": len(rp) - 1, "m": len(ci), "alpha": ALPHA, "lambda": LAMBDA, "queries_per_step": 1},
+        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if ws > 1:
+        dist.barrier()
+    import paper_2101_03652_gb300 as P
+
+    rp, ci, src, kt = make_inputs(args.workload, rank)
+    n, m, k = len(rp) - 1, len(ci), len(src)
+    g = P.Graph(rp, ci)
+    stream = torch.cuda.current_stream()
+    out = torch.empty((k, n), dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    opts = dict(lam=LAMBDA, alpha=ALPHA, k_tile=kt)
+
+    def step(out_buf):
+        return g.query(src, P.PPR_HP, out_pi=out_buf, **opts)[1]
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(out)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sweep_ms, sweep_launches, launches, sweeps = 0.0, 0, 0, []
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            st = step(out)
+            ev[i][1].record(stream)
+            sweep_ms += st[0]["ms_sweep"]
+            sweep_launches += st[0]["sweep_launches"]
+            launches += st[0]["kernel_launches"]
+            sweeps.append(st[0]["sweeps"])
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # end to end: host source ids in, host (pinned) PPR vectors out, copies inside the timed region
+    host_out = torch.empty((k, n), dtype=torch.float64, pin_memory=True)
+    e2e_steps = max(1, min(args.steps, 5))
+    flush.zero_()
+    step(host_out)
+    torch.cuda.synchronize()
+    e2e_total = 0.0
+    for _ in range(e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        step(host_out)
+        e2e_total += time.perf_counter() - t
+    if ws > 1:
+        t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+
+    # sanity of the last answers (the parity tests check them against the oracle)
+    pi0 = out[0].double()
+    mass = float(pi0.sum().item())
+    assert abs(1.0 - mass) <= LAMBDA * 1.01, f"mass {mass}"
+
+    if rank != 0:
+        g.close()
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+
+    value = ws * k * args.steps / (total_ms / 1e3)
+    avg_sweep_ms = sweep_ms / max(sweep_launches, 1)
+    per_launch = sweep_bytes(n, m, kt)
+    achieved = per_launch / (avg_sweep_ms / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    cpu = None
+    if ws == 1 and not args.skip_cpu:
+        import oracle as O
+        og = O.Graph(rp, ci)
+        t = time.perf_counter()
+        done = 0
+        while done < 1 or (time.perf_counter() - t < 10 and done < 3):
+            O.powerpush(og, int(src[done]), ALPHA, LAMBDA)
+            done += 1
+        dt = time.perf_counter() - t
+        cpu = {"value": done / dt, "unit": "queries/s", "cores": 1, "kind": "oracle",
+               "sample": f"{done} of the workload's sources, Algorithm 3 in FP64 on one host core"}
+    rec = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64 (Q1.63 fixed point), f64 output",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "graph": f"R-MAT scale {WORKLOADS[args.workload][0]}, "
+                   f"edge factor {WORKLOADS[args.workload][1]}, a/b/c/d 0.57/0.19/0.19/0.05",
+                   "n": n, "m": m, "alpha": ALPHA, "lambda": LAMBDA, "sources_per_step": k, "k_tile": kt,
+                   "l2": "256 MB buffer written between timed steps", "parallelism": f"replicas x{ws}"},
+        "sweeps_per_tile": statistics.median(sweeps),
+        "e2e": {"value": ws * k * e2e_steps / e2e_total, "unit": "queries/s", "h2d_bytes_per_step": 4 * k,
+                "d2h_bytes_per_step": 8 * k * n},
+        "roofline": {"bound": "hbm", "kernel": f"sweep_kernel<{kt}>", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": ncu_traffic(args.workload), "algorithmic_bytes_per_launch": per_launch,
+                     "avg_launch_ms": avg_sweep_ms},
+        "cpu_baseline": cpu,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(rec))
+    g.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat20-k64", choices=sorted(WORKLOADS))
+    ap.add_argument("--skip-cpu", action="store_true", help="omit the oracle CPU baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,134 @@
+/*
+ * ppr.h — C ABI of the GB300 single-source Personalized PageRank library.
+ *
+ * Method: Wu, Gan, Wei, Zhang, "Unifying the Global and Local Approaches: An
+ * Efficient Power Iteration with Forward Push", SIGMOD'21 (arXiv 2101.03652).
+ *
+ *   PPR pi(s, t): probability that an alpha-random walk from s stops at t
+ *   (Sec. 2); the vector pi_s solves pi_s = alpha e_s + (1-alpha) pi_s P (Eq. 1)
+ *   with P_v = A_v / d_v.
+ *   HP-SSPPR (Sec. 2): return pi_hat with ||pi_hat - pi_s||_1 <= lambda.
+ *   Approx-SSPPR (Sec. 2): |pi_hat(s,v) - pi(s,v)| <= eps pi(s,v) for every
+ *   pi(s,v) >= mu, with probability 1 - 1/n (SpeedPPR, Algorithm 4).
+ *
+ * Graphs are directed CSR: row_ptr int64[n+1] (row_ptr[0] = 0, non-decreasing),
+ * col_idx int32[m], out-neighbours of v in col_idx[row_ptr[v] .. row_ptr[v+1]).
+ * Every node needs out-degree >= 1 (no dead ends, Sec. 2); rows must be sorted
+ * ascending with no duplicates and no self-loops; m < 2^31.
+ *
+ * All functions return a ppr_status (negative on error); ppr_last_error()
+ * gives a thread-local message.  On PPR_ERR_ARG / PPR_ERR_GRAPH nothing is
+ * written.  The library never falls back to the CPU: without a usable CUDA
+ * device every call returns PPR_ERR_CUDA.
+ */
+#ifndef PPR_GB300_H
+#define PPR_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ppr_graph ppr_graph; /* opaque; owns the device copy of the graph */
+
+typedef enum {
+  PPR_OK = 0,
+  PPR_ERR_ARG = -1,           /* bad argument (range, null pointer, unknown mode) */
+  PPR_ERR_GRAPH = -2,         /* graph violates the CSR / no-dead-end contract */
+  PPR_ERR_OOM = -3,           /* device or host allocation failed */
+  PPR_ERR_NOT_CONVERGED = -4, /* a bounded device loop hit its limit */
+  PPR_ERR_CUDA = -5,          /* CUDA runtime error or no device */
+  PPR_ERR_ADMIT = -6          /* not enough free device memory for the batch state */
+} ppr_status;
+
+typedef enum {
+  PPR_HP = 0,     /* high precision: ||pi_hat - pi||_1 <= lambda (PowerPush, Algorithm 3) */
+  PPR_APPROX = 1  /* approximate: SpeedPPR, Algorithm 4 (FP32 push + Philox walks) */
+} ppr_mode;
+
+typedef struct {
+  double alpha;            /* stop probability of the alpha-random walk, in (0,1) (Sec. 2) */
+  double lambda;           /* HP l1 target, > 0 (Sec. 2 uses min(1/m, 1e-8)) */
+  double eps;              /* APPROX relative error, > 0 */
+  double mu;               /* APPROX value threshold; 0 means 1/n */
+  uint64_t seed;           /* APPROX: Philox-4x32-10 key for the walks */
+  int32_t k_tile;          /* sources solved together per pass: 1,2,4,8; 0 = auto */
+  int32_t epoch_num;       /* dense phase: 0 = push every node each sweep (SimFwdPush,
+                              Sec. 4.1); >0 = Algorithm 3's epochs with thresholds
+                              lambda^(i/epoch_num)/m */
+  int64_t switch_edges;    /* queue->sweep switch (Algorithm 3 line "Q.size() <=
+                              scanThreshold"): switch once a frontier level holds more
+                              than this many out-edges over the tile; -1 = auto, 0 = no
+                              queue phase (sweeps from the start) */
+  int32_t max_sweeps;      /* bound on dense sweeps; 0 = 4*ceil(ln lambda/ln(1-alpha))+64 */
+  int32_t reserved;
+  const void* warm_start;  /* reserved for a learned initial estimate; must be NULL */
+} ppr_query_opts;
+
+typedef struct {
+  int32_t sweeps;              /* dense sweeps run for this source's tile */
+  int32_t levels;              /* frontier levels (queue phase) */
+  int64_t edges_pushed;        /* out-edges scattered in the queue phase (this source) */
+  int64_t edges_swept;         /* in-edges gathered by dense sweeps (m per sweep) */
+  int64_t walks;               /* APPROX: random walks started */
+  int64_t walk_steps;          /* APPROX: total walk moves */
+  double initial_l1_residual;  /* ||r||_1 when the dense phase started */
+  double final_l1_residual;    /* certified bound on ||pi - pi_hat||_1 (HP) */
+  double mass_deficit;         /* 1 - sum(pi_hat); equals ||r||_1 for a zero start */
+  double ms_push;               /* device time of the queue phase (whole call) */
+  double ms_sweep;              /* device time of the sweep kernels alone (whole call) */
+  double ms_walk;               /* APPROX: device time of the walk phase */
+  double ms_total;              /* device time of the whole call */
+  int64_t kernel_launches;      /* kernels this call launched */
+  int64_t sweep_launches;       /* of which sweep-kernel launches */
+} ppr_stats;
+
+/* Fill opts with defaults: alpha 0.2, lambda 1e-8, eps 0.5, mu 0 (=1/n),
+ * seed 0x5eed, k_tile 0, epoch_num 0, switch_edges -1, max_sweeps 0. */
+void ppr_default_opts(ppr_query_opts* opts);
+
+/*
+ * Copy a CSR graph (host arrays; the caller keeps ownership) to the device.
+ * The library stores out- and in-adjacency (the in-CSR is the transpose used
+ * by pull sweeps, Algorithm 3's scans), relabelled by in-degree so that rows
+ * of similar length are contiguous.  Work is enqueued on `cuda_stream`
+ * (cudaStream_t or NULL) and completed before return.
+ * Errors: PPR_ERR_ARG (null pointers, n < 1), PPR_ERR_GRAPH (contract above),
+ * PPR_ERR_OOM, PPR_ERR_CUDA.
+ */
+ppr_status ppr_graph_load(const int64_t* row_ptr, const int32_t* col_idx, int64_t n, int64_t m,
+                          void* cuda_stream, ppr_graph** out);
+
+/*
+ * Answer k single-source queries.  src: host int32[k], each in [0, n);
+ * duplicates allowed; src order is the output row order.
+ *   out_pi  : k x n row-major float64, device or host memory (caller-owned).
+ *   out_r   : optional (NULL) k x n float64, device or host: HP = the push
+ *             residual r = (alpha e_s + (1-alpha) pi_hat P - pi_hat)/alpha of the
+ *             returned pi_hat; APPROX = the FP32 residue the walks started from.
+ *   out_walk_counts: optional k x n uint32 (APPROX only) walk endpoint counts.
+ *   stats   : optional host array of k entries.
+ * HP mode follows Algorithm 3 (frontier push, then sweeps); APPROX follows
+ * Algorithm 4.  Work runs on `cuda_stream`; the call returns after the stream
+ * has finished the query.  Errors: PPR_ERR_ARG, PPR_ERR_ADMIT (state does not
+ * fit in free device memory), PPR_ERR_NOT_CONVERGED, PPR_ERR_OOM, PPR_ERR_CUDA.
+ */
+ppr_status ppr_sssp_query(ppr_graph* g, const int32_t* src, int32_t k, ppr_mode mode,
+                          const ppr_query_opts* opts, double* out_pi, double* out_r,
+                          uint32_t* out_walk_counts, ppr_stats* stats, void* cuda_stream);
+
+/* Release the graph and every device buffer it owns; NULL is allowed. */
+void ppr_free(ppr_graph* g);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* ppr_last_error(void);
+
+/* Graph sizes: n, m as loaded. */
+int64_t ppr_graph_n(const ppr_graph* g);
+int64_t ppr_graph_m(const ppr_graph* g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PPR_GB300_H */

@@ -1,0 +1,196 @@
+"""ctypes binding of the C ABI declared in include/ppr.h.
+
+Argument marshalling only: every step of a query runs in the CUDA library.
+There is no CPU fallback; if the library cannot be loaded or no GPU is
+present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+PPR_OK, PPR_ERR_ARG, PPR_ERR_GRAPH, PPR_ERR_OOM = 0, -1, -2, -3
+PPR_ERR_NOT_CONVERGED, PPR_ERR_CUDA, PPR_ERR_ADMIT = -4, -5, -6
+PPR_HP, PPR_APPROX = 0, 1
+
+STATUS_NAMES = {0: "PPR_OK", -1: "PPR_ERR_ARG", -2: "PPR_ERR_GRAPH", -3: "PPR_ERR_OOM",
+                -4: "PPR_ERR_NOT_CONVERGED", -5: "PPR_ERR_CUDA", -6: "PPR_ERR_ADMIT"}
+
+
+class PPRError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class ppr_query_opts(ctypes.Structure):
+    _fields_ = [
+        ("alpha", ctypes.c_double),
+        ("lambda_", ctypes.c_double),
+        ("eps", ctypes.c_double),
+        ("mu", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("k_tile", ctypes.c_int32),
+        ("epoch_num", ctypes.c_int32),
+        ("switch_edges", ctypes.c_int64),
+        ("max_sweeps", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("warm_start", ctypes.c_void_p),
+    ]
+
+
+class ppr_stats(ctypes.Structure):
+    _fields_ = [
+        ("sweeps", ctypes.c_int32),
+        ("levels", ctypes.c_int32),
+        ("edges_pushed", ctypes.c_int64),
+        ("edges_swept", ctypes.c_int64),
+        ("walks", ctypes.c_int64),
+        ("walk_steps", ctypes.c_int64),
+        ("initial_l1_residual", ctypes.c_double),
+        ("final_l1_residual", ctypes.c_double),
+        ("mass_deficit", ctypes.c_double),
+        ("ms_push", ctypes.c_double),
+        ("ms_sweep", ctypes.c_double),
+        ("ms_walk", ctypes.c_double),
+        ("ms_total", ctypes.c_double),
+        ("kernel_launches", ctypes.c_int64),
+        ("sweep_launches", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# every symbol include/ppr.h declares, with its ctypes signature
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "ppr_default_opts": (None, [ctypes.POINTER(ppr_query_opts)]),
+    "ppr_graph_load": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, ctypes.POINTER(_P)]),
+    "ppr_sssp_query": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int, ctypes.POINTER(ppr_query_opts),
+                                      _P, _P, _P, _P, _P]),
+    "ppr_free": (None, [_P]),
+    "ppr_last_error": (ctypes.c_char_p, []),
+    "ppr_graph_n": (ctypes.c_int64, [_P]),
+    "ppr_graph_m": (ctypes.c_int64, [_P]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(build: bool = True):
+    """Load libppr_gb300.so (building it first if sources changed)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build else _build.LIB
+            if not os.path.exists(path):
+                raise ImportError(f"CUDA library not built: {path}")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def ppr_last_error() -> str:
+    return load_library().ppr_last_error().decode()
+
+
+def _check(status: int):
+    if status != PPR_OK:
+        raise PPRError(status, ppr_last_error())
+
+
+def ppr_default_opts(**kw) -> ppr_query_opts:
+    o = ppr_query_opts()
+    load_library().ppr_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, "lambda_" if k == "lam" else k, v)
+    return o
+
+
+def _ptr(x):
+    """(address, is_device) of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    assert x.is_contiguous()
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+def ppr_graph_load(row_ptr: np.ndarray, col_idx: np.ndarray, stream=None) -> int:
+    """Upload a CSR graph; returns the opaque graph handle (an int)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(load_library().ppr_graph_load(rp.ctypes.data, ci.ctypes.data, len(rp) - 1, len(ci), _stream(stream),
+                                         ctypes.byref(h)))
+    return h.value
+
+
+def ppr_sssp_query(graph: int, src, mode: int, opts: ppr_query_opts, out_pi, out_r=None, out_walk_counts=None,
+                   stats: bool = True, stream=None):
+    """Run k queries; out_* are torch tensors (CUDA or CPU) or numpy arrays of shape (k, n)."""
+    s = np.ascontiguousarray(src, dtype=np.int32)
+    st = (ppr_stats * len(s))() if stats else None
+    _check(load_library().ppr_sssp_query(graph, s.ctypes.data, len(s), mode, ctypes.byref(opts), _ptr(out_pi),
+                                         _ptr(out_r), _ptr(out_walk_counts), st, _stream(stream)))
+    return [x.as_dict() for x in st] if stats else None
+
+
+def ppr_free(graph: int):
+    if graph:
+        load_library().ppr_free(graph)
+
+
+class Graph:
+    """Owner of a device graph: ``Graph(row_ptr, col_idx).query(src, ...)``."""
+
+    def __init__(self, row_ptr, col_idx, stream=None):
+        self.n = len(row_ptr) - 1
+        self.m = len(col_idx)
+        self.handle = ppr_graph_load(row_ptr, col_idx, stream)
+
+    def close(self):
+        if self.handle:
+            ppr_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def query(self, src, mode: int = PPR_HP, out_pi=None, out_r=None, out_walk_counts=None, stream=None, **opts):
+        """Returns (pi, stats); pi is a (k, n) float64 CUDA tensor unless out_pi is given."""
+        import torch
+        k = len(src)
+        if out_pi is None:
+            out_pi = torch.empty((k, self.n), dtype=torch.float64, device="cuda")
+        o = ppr_default_opts(**opts)
+        stats = ppr_sssp_query(self.handle, src, mode, o, out_pi, out_r, out_walk_counts, True, stream)
+        return out_pi, stats

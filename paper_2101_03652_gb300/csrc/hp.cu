@@ -1,0 +1,848 @@
+// High-precision SSPPR on the GPU: Algorithm 3 (PowerPush) restated for GB300.
+//
+// State.  Residues, reserves and estimates are unsigned Q1.63 fixed point
+// (value = raw * 2^-63) in 64-bit integers.  Sums are then exact and
+// independent of the order in which threads add, mass is conserved bit for
+// bit by every push, and no FP64 arithmetic runs per edge (GB300's FP64 rate
+// is a small fraction of its integer rate).  Resolution is 1.1e-19 per value,
+// far below the l1 targets (>= 1e-12) the library accepts.
+//
+// Queue phase (Algorithm 3, first loop; Algorithm 2's iterations S^(j)).
+// A frontier holds (node, column) pairs; one warp pushes one pair: it takes
+// the residue with an atomic exchange (asynchronous pushes, Sec. 5), credits
+// alpha*rho to the reserve and scatters (1-alpha)*rho/d_v to the out-neighbours
+// with 64-bit integer atomics (the division remainder goes one unit at a time
+// to the first neighbours, so no mass is lost).  A neighbour whose residue
+// crosses d_u * r_max joins the next level; a per-level stamp plays the role of
+// "u not in Q", and the warp appends its new entries with one atomic (ballot +
+// popcount + prefix).  The phase ends when every column has sum(r) <= lambda,
+// the frontier empties, or a level's out-edges exceed the switch threshold
+// (the GPU counterpart of |Q| > scanThreshold).
+//
+// Sweep phase (Algorithm 3, epochs of full scans).  A full pass that pushes
+// every node at once is SimFwdPush (Sec. 4.1, Eq. 7), equal to PowItr by
+// Lemma 1.  It is run in the estimate form x <- alpha e_s + (1-alpha) x P:
+// with x0 = reserve + alpha*residue the k-th pass equals k simultaneous pushes,
+// and ||x_{j+1} - x_j||_1 / alpha is the l1 norm of the residue of x_j.  Each
+// pass stores z = (1-alpha) x / d so that a row u of the in-CSR only sums the
+// z of its in-neighbours (a gather, no per-edge multiply).  Because the
+// residue contracts by (1-alpha) per pass, the number of passes to reach
+// lambda is predicted and launched without per-pass host round trips; the
+// last pass's measured residue certifies the result.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "ppr_internal.cuh"
+
+namespace ppr {
+
+constexpr unsigned kFull = 0xffffffffu;
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 mulhi_round(u64 x, u64 w) {
+  u64 hi = __umul64hi(x, w);
+  u64 lo = x * w;
+  return hi + (lo >> 63);
+}
+
+// ------------------------------------------------------------ queue phase
+struct PushArgs {
+  const uint32_t* front;
+  uint32_t n_front;
+  const int32_t* out_rp;
+  const int32_t* out_ci;
+  const int32_t* deg;
+  u64* r;
+  u64* pi;
+  uint32_t* stamp;
+  uint32_t next_stamp;
+  uint32_t* next_front;
+  u64* ent_share;   // per frontier entry: (1-alpha) rho / d (floor)
+  uint32_t* ent_rem; // per frontier entry: remainder of that division
+  u64* chunks;      // (entry << 32 | first edge) records, kPushChunk edges each
+  u64* counters;    // [0] next size, [1] next out-edges, [2] chunks, [3+c] stopped mass,
+                    // [3+KT+c] edges pushed
+  u64 alpha64;      // alpha * 2^64
+  u64 rmax_raw;     // r_max in Q1.63 units
+};
+constexpr int kPushChunk = 256;
+
+// Phase A: one thread per frontier entry takes the residue (atomic exchange,
+// so pushes landing meanwhile are not lost), credits alpha*rho to the reserve
+// and emits one chunk record per kPushChunk out-edges.
+template <int KT>
+__global__ void __launch_bounds__(256) push_take_kernel(PushArgs a) {
+  const int lane = threadIdx.x & 31;
+  for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < a.n_front; i0 += gridDim.x * blockDim.x) {
+    const uint32_t i = i0 + threadIdx.x;
+    uint32_t nch = 0;
+    if (i < a.n_front) {
+      const uint32_t idx = a.front[i];
+      const uint32_t v = idx / KT;
+      const int c = idx % KT;
+      const int32_t d = __ldg(&a.deg[v]);
+      u64 rho = 0;
+      u64 cur = *(volatile u64*)&a.r[idx];
+      if (cur > (u64)d * a.rmax_raw) rho = atomicExch(&a.r[idx], 0ull);
+      if (rho) {
+        const u64 stop = __umul64hi(rho, a.alpha64);  // alpha * rho
+        const u64 rest = rho - stop;                  // (1 - alpha) * rho, exact complement
+        const u64 share = rest / (u64)d;
+        a.ent_share[i] = share;
+        a.ent_rem[i] = (uint32_t)(rest - share * (u64)d);
+        a.pi[idx] += stop;
+        atomicAdd(&a.counters[3 + c], stop);
+        atomicAdd(&a.counters[3 + KT + c], (u64)d);
+        nch = (uint32_t)((d + kPushChunk - 1) / kPushChunk);
+      }
+    }
+    // warp-aggregated append of the chunk records
+    uint32_t incl = nch;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      uint32_t t = __shfl_up_sync(kFull, incl, off);
+      if (lane >= off) incl += t;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    u64 base = 0;
+    if (lane == 31 && total) base = atomicAdd(&a.counters[2], (u64)total);
+    base = __shfl_sync(kFull, base, 31);
+    for (uint32_t q = 0; q < nch; ++q)
+      a.chunks[base + incl - nch + q] = ((u64)i << 32) | (u64)(q * kPushChunk);
+  }
+}
+
+// Phase B: one warp per chunk scatters (1-alpha) rho / d to up to kPushChunk
+// out-neighbours (the first `rem` neighbours of the row get one extra unit, so
+// the push conserves mass exactly).  A neighbour whose residue crosses
+// d_u * r_max joins the next frontier once per level (stamp), appended with
+// one atomic per warp (ballot + popcount + prefix).
+template <int KT>
+__global__ void __launch_bounds__(256) push_scatter_kernel(PushArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const u64 nchunks = *(volatile u64*)&a.counters[2];
+  for (u64 ch = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; ch < nchunks; ch += nwarps) {
+    const u64 rec = a.chunks[ch];
+    const uint32_t i = (uint32_t)(rec >> 32);
+    const int32_t j0 = (int32_t)(rec & 0xffffffffu);
+    const uint32_t idx = a.front[i];
+    const uint32_t v = idx / KT;
+    const int c = idx % KT;
+    const int32_t e0 = __ldg(&a.out_rp[v]);
+    const int32_t d = __ldg(&a.deg[v]);
+    const u64 share = a.ent_share[i];
+    const uint32_t rem = a.ent_rem[i];
+    const int32_t j1 = min(d, j0 + kPushChunk);
+    for (int32_t base = j0; base < j1; base += 32) {
+      const int32_t j = base + lane;
+      bool app = false;
+      uint32_t uidx = 0;
+      int32_t du = 0;
+      if (j < j1) {
+        const int32_t u = __ldg(&a.out_ci[e0 + j]);
+        const u64 add = share + ((uint32_t)j < rem ? 1ull : 0ull);
+        uidx = (uint32_t)u * KT + c;
+        if (add) {
+          const u64 old = atomicAdd(&a.r[uidx], add);
+          du = __ldg(&a.deg[u]);
+          const u64 thr = (u64)du * a.rmax_raw;
+          if (old + add > thr && old <= thr) app = atomicExch(&a.stamp[uidx], a.next_stamp) != a.next_stamp;
+        }
+      }
+      const unsigned mask = __ballot_sync(kFull, app);
+      if (mask) {
+        u64 esum = app ? (u64)du : 0ull;
+#pragma unroll
+        for (int off = 16; off; off >>= 1) esum += __shfl_xor_sync(kFull, esum, off);
+        u64 pos0 = 0;
+        if (lane == 0) {
+          pos0 = atomicAdd(&a.counters[0], (u64)__popc(mask));
+          atomicAdd(&a.counters[1], esum);
+        }
+        pos0 = __shfl_sync(kFull, pos0, 0);
+        if (app) a.next_front[pos0 + __popc(mask & ((1u << lane) - 1u))] = uidx;
+      }
+    }
+  }
+}
+
+template <int KT>
+__global__ void init_sources_kernel(const int32_t* __restrict__ src_new, int ncols, u64* r, uint32_t* stamp,
+                                    uint32_t epoch, uint32_t* front) {
+  int c = threadIdx.x;
+  if (c < ncols) {
+    uint32_t idx = (uint32_t)src_new[c] * KT + c;
+    r[idx] = kFixOneRaw;
+    stamp[idx] = epoch;
+    front[c] = idx;
+  }
+}
+
+// x0 = reserve + alpha * residue; z0 = (1-alpha) x0 / d
+template <int KT>
+__global__ void convert_kernel(int64_t n, const u64* __restrict__ r, const u64* __restrict__ pi,
+                               const uint64_t* __restrict__ omega, u64 alpha64, u64* __restrict__ z) {
+  const int64_t total = n * KT;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    u64 x0 = pi[i] + __umul64hi(r[i], alpha64);
+    z[i] = mulhi_round(x0, omega[i / KT]);
+  }
+}
+
+// ------------------------------------------------------------ sweep phase
+struct SweepArgs {
+  int32_t n;         // rows processed: all rows, or only rows with in-degree > 0 once
+                     // the others hold their final (constant) value in both buffers
+  const int32_t* in_rp;
+  const int32_t* in_ci;
+  const uint64_t* omega;
+  const float* invw;
+  const u64* z_in;
+  u64* z_out;
+  u64* x_out;        // optional: the estimate x of this pass
+  int32_t src[16];   // tile's sources (new ids), -1 for unused columns
+  u64 alpha_raw;     // alpha in Q1.63
+  double* resid;     // [KT] sums of |x_new - x_old| in raw units (this pass)
+  int32_t n_heavy, medium_end;
+  int32_t n_pieces, piece_edges;
+  const int32_t* piece_row;
+  const int32_t* piece_e0;
+  const int32_t* heavy_npieces;
+  u64* heavy_acc;
+  unsigned int* heavy_cnt;
+  int32_t nb_heavy, nb_medium;
+};
+
+template <int KT>
+struct Lay {
+  static constexpr int V = KT >= 2 ? 2 : 1;  // uint64 per lane load (16 B when 2)
+  static constexpr int L = KT / V;           // lanes covering one row of the tile
+  static constexpr int EPW = 32 / L;         // edges a warp gathers per step
+};
+
+template <int V>
+__device__ __forceinline__ void ld_vec(const u64* p, u64 (&v)[V]) {
+  if constexpr (V == 2) {
+    ulonglong2 t = __ldg(reinterpret_cast<const ulonglong2*>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+  } else {
+    v[0] = __ldg(p);
+  }
+}
+template <int V>
+__device__ __forceinline__ void st_vec(u64* p, const u64 (&v)[V]) {
+  if constexpr (V == 2) {
+    *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(v[0], v[1]);
+  } else {
+    p[0] = v[0];
+  }
+}
+
+// finish row u for the V columns of `slot`: x = sum + alpha [u == s], z = x w
+template <int KT>
+__device__ __forceinline__ void row_epilogue(const SweepArgs& a, int u, int slot, const u64 (&acc)[Lay<KT>::V],
+                                             float (&res)[Lay<KT>::V]) {
+  constexpr int V = Lay<KT>::V;
+  const u64 om = __ldg(&a.omega[u]);
+  const float iw = __ldg(&a.invw[u]);
+  u64 zo[V], zn[V], xn[V];
+  ld_vec<V>(a.z_in + (size_t)u * KT + slot * V, zo);
+#pragma unroll
+  for (int q = 0; q < V; ++q) {
+    const int c = slot * V + q;
+    xn[q] = acc[q] + (u == a.src[c] ? a.alpha_raw : 0ull);
+    zn[q] = mulhi_round(xn[q], om);
+    const u64 dz = zn[q] > zo[q] ? zn[q] - zo[q] : zo[q] - zn[q];
+    res[q] += (float)dz * iw;
+  }
+  st_vec<V>(a.z_out + (size_t)u * KT + slot * V, zn);
+  if (a.x_out) st_vec<V>(a.x_out + (size_t)u * KT + slot * V, xn);
+}
+
+// Sum z over in-edges [e_begin, e_end) of one row; the warp's lanes cover
+// EPW edges per step (L lanes per edge) and UNR steps are issued before any
+// is consumed, so each lane keeps UNR independent gathers in flight.  The
+// loop bound is warp-uniform; lanes past the end are predicated off.
+template <int KT, int UNR>
+__device__ __forceinline__ void gather_warp(const SweepArgs& a, int e_begin, int e_end, int lane, int slot,
+                                            u64 (&acc)[Lay<KT>::V]) {
+  constexpr int V = Lay<KT>::V, L = Lay<KT>::L, EPW = Lay<KT>::EPW;
+  for (int base = e_begin; base < e_end; base += EPW * UNR) {
+    int v[UNR];
+#pragma unroll
+    for (int q = 0; q < UNR; ++q) {
+      const int e = base + q * EPW + lane / L;
+      v[q] = e < e_end ? __ldg(&a.in_ci[e]) : -1;
+    }
+    u64 t[UNR][V];
+#pragma unroll
+    for (int q = 0; q < UNR; ++q) {
+      if (v[q] >= 0) {
+        ld_vec<V>(a.z_in + (size_t)v[q] * KT + slot * V, t[q]);
+      } else {
+#pragma unroll
+        for (int w = 0; w < V; ++w) t[q][w] = 0;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < UNR; ++q)
+#pragma unroll
+      for (int w = 0; w < V; ++w) acc[w] += t[q][w];
+  }
+}
+
+template <int KT>
+__global__ void __launch_bounds__(256, 4) sweep_kernel(SweepArgs a) {
+  constexpr int V = Lay<KT>::V, L = Lay<KT>::L;
+  constexpr int UNR = 4;
+  const int lane = threadIdx.x & 31;
+  const int slot = lane % L;
+  float res[V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) res[q] = 0.f;
+
+  if ((int)blockIdx.x < a.nb_heavy) {
+    // split rows: one warp per piece, partial sums combined with integer atomics;
+    // the last piece of a row to arrive finishes it
+    const int nw = a.nb_heavy * (blockDim.x >> 5);
+    for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < a.n_pieces; p += nw) {
+      const int u = a.piece_row[p];
+      const int e0 = a.piece_e0[p];
+      const int e1 = min(e0 + a.piece_edges, __ldg(&a.in_rp[u + 1]));
+      u64 acc[V] = {};
+      gather_warp<KT, UNR>(a, e0, e1, lane, slot, acc);
+#pragma unroll
+      for (int off = L; off < 32; off <<= 1)
+#pragma unroll
+        for (int q = 0; q < V; ++q) acc[q] += __shfl_xor_sync(kFull, acc[q], off);
+      if (lane < L)
+#pragma unroll
+        for (int q = 0; q < V; ++q) atomicAdd(&a.heavy_acc[(size_t)u * KT + slot * V + q], acc[q]);
+      __threadfence();
+      unsigned ticket = 0;
+      if (lane == 0) ticket = atomicAdd(&a.heavy_cnt[u], 1u);
+      ticket = __shfl_sync(kFull, ticket, 0);
+      if (ticket == (unsigned)a.heavy_npieces[u] - 1u) {
+        __threadfence();
+        if (lane < L) {
+          u64 tot[V];
+#pragma unroll
+          for (int q = 0; q < V; ++q) tot[q] = atomicExch(&a.heavy_acc[(size_t)u * KT + slot * V + q], 0ull);
+          row_epilogue<KT>(a, u, slot, tot, res);
+        }
+        if (lane == 0) atomicExch(&a.heavy_cnt[u], 0u);
+      }
+    }
+  } else if ((int)blockIdx.x < a.nb_heavy + a.nb_medium) {
+    // medium rows: one warp per row
+    const int nw = a.nb_medium * (blockDim.x >> 5);
+    const int w0 = ((blockIdx.x - a.nb_heavy) * blockDim.x + threadIdx.x) >> 5;
+    for (int u = a.n_heavy + w0; u < a.medium_end; u += nw) {
+      u64 acc[V] = {};
+      gather_warp<KT, UNR>(a, __ldg(&a.in_rp[u]), __ldg(&a.in_rp[u + 1]), lane, slot, acc);
+#pragma unroll
+      for (int off = L; off < 32; off <<= 1)
+#pragma unroll
+        for (int q = 0; q < V; ++q) acc[q] += __shfl_xor_sync(kFull, acc[q], off);
+      if (lane < L) row_epilogue<KT>(a, u, slot, acc, res);
+    }
+  } else {
+    // light rows: L lanes per row, 32/L consecutive rows per warp; the trip
+    // count is the warp's largest row (rows are sorted by length, so the
+    // rows of one warp have nearly equal length)
+    constexpr int RPW = 32 / L;
+    const int nwl = (gridDim.x - a.nb_heavy - a.nb_medium) * (blockDim.x >> 5);
+    const int wl = ((blockIdx.x - a.nb_heavy - a.nb_medium) * blockDim.x + threadIdx.x) >> 5;
+    for (int row0 = a.medium_end + wl * RPW; row0 < a.n; row0 += nwl * RPW) {
+      const int u = row0 + lane / L;
+      const bool live = u < a.n;
+      const int e0 = live ? __ldg(&a.in_rp[u]) : 0;
+      const int d = live ? __ldg(&a.in_rp[u + 1]) - e0 : 0;
+      const int dmax = __reduce_max_sync(kFull, d);
+      u64 acc[V] = {};
+      for (int j = 0; j < dmax; j += UNR) {
+        int v[UNR];
+#pragma unroll
+        for (int q = 0; q < UNR; ++q) v[q] = (j + q < d) ? __ldg(&a.in_ci[e0 + j + q]) : -1;
+        u64 t[UNR][V];
+#pragma unroll
+        for (int q = 0; q < UNR; ++q) {
+          if (v[q] >= 0) {
+            ld_vec<V>(a.z_in + (size_t)v[q] * KT + slot * V, t[q]);
+          } else {
+#pragma unroll
+            for (int w = 0; w < V; ++w) t[q][w] = 0;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < UNR; ++q)
+#pragma unroll
+          for (int w = 0; w < V; ++w) acc[w] += t[q][w];
+      }
+      if (live) row_epilogue<KT>(a, u, slot, acc, res);
+    }
+  }
+
+  // per-column residual: lanes with equal slot, then warps, then one atomic per column
+  __shared__ float sred[8][16];
+#pragma unroll
+  for (int off = L; off < 32; off <<= 1)
+#pragma unroll
+    for (int q = 0; q < V; ++q) res[q] += __shfl_xor_sync(kFull, res[q], off);
+  const int warp = threadIdx.x >> 5;
+  if (lane < L)
+#pragma unroll
+    for (int q = 0; q < V; ++q) sred[warp][lane * V + q] = res[q];
+  __syncthreads();
+  if (threadIdx.x < KT) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += (double)sred[w][threadIdx.x];
+    atomicAdd(&a.resid[threadIdx.x], sum);
+  }
+}
+
+// out[(col0 + c) * n + o] = x[new(o)][c] as float64; exact per-column sums of x
+template <int KT>
+__global__ void output_kernel(int64_t n, const int32_t* __restrict__ new_of_old, const u64* __restrict__ x,
+                              int ncols, int64_t col0, double* __restrict__ out, u64* mass) {
+  u64 ms[KT];
+#pragma unroll
+  for (int c = 0; c < KT; ++c) ms[c] = 0;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = new_of_old[o];
+#pragma unroll
+    for (int c = 0; c < KT; ++c) {
+      if (c < ncols) {
+        u64 v = x[u * KT + c];
+        ms[c] += v;
+        out[(col0 + c) * n + o] = (double)v * (1.0 / kFixOne);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < KT; ++c) {
+    u64 s = ms[c];
+#pragma unroll
+    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
+    if ((threadIdx.x & 31) == 0 && c < ncols) atomicAdd(&mass[c], s);
+  }
+}
+
+// push residual of the returned estimate: r = (alpha e_s + sum z(v) - x(u)) / alpha
+template <int KT>
+__global__ void residual_kernel(int32_t n, const int32_t* __restrict__ in_rp, const int32_t* __restrict__ in_ci,
+                                const int32_t* __restrict__ old_of_new, const u64* __restrict__ z,
+                                const u64* __restrict__ x, SweepArgs a, int ncols, int64_t col0, double alpha,
+                                double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+    for (int c = 0; c < ncols; ++c) {
+      u64 acc = 0;
+      for (int e = in_rp[u] + lane; e < in_rp[u + 1]; e += 32) acc += z[(size_t)in_ci[e] * KT + c];
+#pragma unroll
+      for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+      if (lane == 0) {
+        u64 xn = acc + (u == a.src[c] ? a.alpha_raw : 0ull);
+        long long diff = (long long)(xn - x[(size_t)u * KT + c]);
+        out[(col0 + c) * (int64_t)n + old_of_new[u]] = (double)diff * (1.0 / kFixOne) / alpha;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ host engine
+static int sm_count() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
+    if (cached <= 0) cached = 1;
+  }
+  return cached;
+}
+
+struct Plan {
+  int kt;
+  int32_t medium_end;
+  int nb_heavy, nb_medium, nb_light;
+};
+
+static Plan make_plan(const ppr_graph* g, int kt, int blocks_per_sm) {
+  Plan p;
+  p.kt = kt;
+  const int light_max = 16;
+  // rows [n_heavy, medium_end) have in-degree in (light_max, heavy_deg]
+  const std::vector<int32_t>& d = g->h_in_deg_sorted;
+  int32_t lo = g->n_heavy, hi = (int32_t)g->n;
+  while (lo < hi) {
+    int32_t mid = lo + (hi - lo) / 2;
+    if (d[mid] > light_max) lo = mid + 1; else hi = mid;
+  }
+  p.medium_end = lo;
+  // split a persistent-size grid by estimated work (edges, plus a row overhead)
+  double e_heavy = 0, e_med = 0, e_light = 0;
+  for (int32_t u = 0; u < g->n_heavy; ++u) e_heavy += d[u];
+  for (int32_t u = g->n_heavy; u < p.medium_end; ++u) e_med += d[u] + 8;
+  for (int32_t u = p.medium_end; u < (int32_t)g->n; ++u) e_light += d[u] + 2;
+  const int total = sm_count() * blocks_per_sm;  // every block resident at once
+  double sum = e_heavy + e_med + e_light;
+  p.nb_heavy = g->n_pieces > 0 ? std::max(1, (int)std::lround(total * e_heavy / sum)) : 0;
+  p.nb_medium = p.medium_end > g->n_heavy ? std::max(1, (int)std::lround(total * e_med / sum)) : 0;
+  p.nb_light = std::max(1, total - p.nb_heavy - p.nb_medium);
+  return p;
+}
+
+template <int KT>
+static void launch_sweep(const SweepArgs& a, const Plan& p, cudaStream_t st) {
+  static bool configured = false;
+  if (!configured) {
+    // the kernel needs almost no shared memory: give the SM's storage to L1,
+    // which caches the gathered rows of the most-referenced nodes
+    cudaFuncSetAttribute(sweep_kernel<KT>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    configured = true;
+  }
+  sweep_kernel<KT><<<p.nb_heavy + p.nb_medium + p.nb_light, 256, 0, st>>>(a);
+}
+
+template <int KT>
+static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query_opts& o, double* out_pi,
+                         double* out_r, ppr_stats* stats, cudaStream_t st) {
+  const int64_t n = g->n, m = g->m;
+  const double alpha = o.alpha, lambda = o.lambda;
+  Workspace& ws = g->ws;
+  const size_t cells = (size_t)n * KT;
+  const bool pi_on_host = !is_device_pointer(out_pi);
+  const bool r_on_host = out_r && !is_device_pointer(out_r);
+  const int max_sweeps = o.max_sweeps > 0 ? o.max_sweeps
+                                          : 4 * (int)std::ceil(std::log(lambda) / std::log(1.0 - alpha)) + 64;
+
+  // admission: state for one tile plus staging of host outputs
+  size_t need = 4 * cells * 8 + cells * 4 * 4 + cells * 16 + (size_t)m * KT / kPushChunk * 8 + (size_t)g->n_heavy * KT * 8 + (size_t)max_sweeps * KT * 8;
+  size_t stage_bytes = 0;
+  if (pi_on_host) stage_bytes += (size_t)k * n * 8;
+  if (r_on_host) stage_bytes += (size_t)k * n * 8;
+  {
+    size_t have_bytes = ws.r.bytes + ws.pi.bytes + ws.za.bytes + ws.zb.bytes + ws.stamp.bytes + ws.front_a.bytes +
+                        ws.front_b.bytes + ws.heavy_acc.bytes + ws.resid.bytes + ws.stage.bytes;
+    size_t free_b = 0, total_b = 0;
+    PPR_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    if (need + stage_bytes > free_b + have_bytes) {
+      set_error("admission refused: batch state needs %zu bytes, %zu free", need + stage_bytes, free_b);
+      return PPR_ERR_ADMIT;
+    }
+  }
+  bool fresh_stamp = ws.stamp.bytes < cells * 4;
+  PPR_TRY(ws.r.ensure(cells * 8));
+  PPR_TRY(ws.pi.ensure(cells * 8));
+  PPR_TRY(ws.za.ensure(cells * 8));
+  PPR_TRY(ws.zb.ensure(cells * 8));
+  PPR_TRY(ws.stamp.ensure(cells * 4));
+  PPR_TRY(ws.front_a.ensure(cells * 4));
+  PPR_TRY(ws.front_b.ensure(cells * 4));
+  PPR_TRY(ws.ent_share.ensure(cells * 8));
+  PPR_TRY(ws.ent_rem.ensure(cells * 4));
+  PPR_TRY(ws.chunks.ensure((cells + (size_t)m * KT / kPushChunk + 64) * 8));
+  bool fresh_heavy = ws.heavy_acc.ptr == nullptr || ws.heavy_cnt.ptr == nullptr;
+  PPR_TRY(ws.heavy_acc.ensure(std::max<size_t>((size_t)g->n_heavy * 16 * 8, 8)));
+  PPR_TRY(ws.heavy_cnt.ensure(std::max<size_t>((size_t)g->n_heavy * 4, 4)));
+  PPR_TRY(ws.counters.ensure(4096));
+  PPR_TRY(ws.resid.ensure((size_t)(max_sweeps + 1) * 16 * 8));
+  if (stage_bytes) PPR_TRY(ws.stage.ensure(stage_bytes));
+  if (!ws.pinned) {
+    PPR_CUDA_TRY(cudaMallocHost(&ws.pinned, 65536));
+    ws.pinned_bytes = 65536;
+  }
+  if (fresh_stamp || g->stamp_epoch > 0xF0000000u) {
+    PPR_CUDA_TRY(cudaMemsetAsync(ws.stamp.ptr, 0, ws.stamp.bytes, st));
+    g->stamp_epoch = 0;
+  }
+  if (fresh_heavy) {
+    PPR_CUDA_TRY(cudaMemsetAsync(ws.heavy_acc.ptr, 0, ws.heavy_acc.bytes, st));
+    PPR_CUDA_TRY(cudaMemsetAsync(ws.heavy_cnt.ptr, 0, ws.heavy_cnt.bytes, st));
+  }
+  PPR_TRY(ensure_alpha(g, alpha, st));
+
+  u64* r = ws.r.as<u64>();
+  u64* pi = ws.pi.as<u64>();
+  u64* za = ws.za.as<u64>();
+  u64* zb = ws.zb.as<u64>();
+  u64* counters = ws.counters.as<u64>();
+  double* resid = ws.resid.as<double>();
+  u64* hpin = static_cast<u64*>(ws.pinned);
+  int32_t* d_src = reinterpret_cast<int32_t*>(counters + 256);  // device copy of the tile's sources
+  double* out_pi_dev = pi_on_host ? ws.stage.as<double>() : out_pi;
+  double* out_r_dev = !out_r ? nullptr : (r_on_host ? ws.stage.as<double>() + (pi_on_host ? (size_t)k * n : 0) : out_r);
+
+  const u64 alpha64 = (u64)(alpha * 18446744073709551616.0);
+  const u64 alpha_raw = (u64)(alpha * kFixOne);
+  const double rmax = lambda / (double)m;
+  const u64 rmax_raw = (u64)std::max(1.0, std::floor(rmax * kFixOne));
+  const u64 lambda_raw = (u64)std::floor(lambda * kFixOne);
+  const int64_t switch_edges = o.switch_edges >= 0 ? o.switch_edges : (int64_t)(0.02 * (double)m * KT);
+  int bps = 0;
+  PPR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, sweep_kernel<KT>, 256, 0));
+  const Plan plan = make_plan(g, KT, std::max(bps, 1));
+  const int grid_ew = sm_count() * 8;
+
+  cudaEvent_t ev0, ev1, ev2, es0, es1;
+  PPR_CUDA_TRY(cudaEventCreate(&ev0));
+  PPR_CUDA_TRY(cudaEventCreate(&ev1));
+  PPR_CUDA_TRY(cudaEventCreate(&ev2));
+  PPR_CUDA_TRY(cudaEventCreate(&es0));
+  PPR_CUDA_TRY(cudaEventCreate(&es1));
+  float ms_push = 0.f, ms_sweep = 0.f, ms_total = 0.f;
+  int64_t launches = 0, sweep_launches = 0;
+  int32_t n_nz = 0;  // rows with in-degree > 0 are the first n_nz rows
+  {
+    const std::vector<int32_t>& d = g->h_in_deg_sorted;
+    int32_t lo = 0, hi = (int32_t)n;
+    while (lo < hi) {
+      int32_t mid = lo + (hi - lo) / 2;
+      if (d[mid] > 0) lo = mid + 1; else hi = mid;
+    }
+    n_nz = lo;
+  }
+  ppr_status status = PPR_OK;
+
+  for (int32_t t0 = 0; t0 < k && status == PPR_OK; t0 += KT) {
+    const int ncols = std::min<int32_t>(KT, k - t0);
+    int32_t src_new[16];
+    for (int c = 0; c < 16; ++c) src_new[c] = c < ncols ? g->h_new_of_old[src[t0 + c]] : -1;
+    PPR_CUDA_TRY(cudaEventRecord(ev0, st));
+
+    // ---- queue phase
+    std::vector<double> rsum(KT, 0.0), r0(KT, 1.0);
+    std::vector<int64_t> pushed(KT, 0);
+    int levels = 0;
+    bool all_done = false;
+    bool have_state = false;  // (r, pi) hold a push state
+    if (switch_edges != 0) {
+      PPR_CUDA_TRY(cudaMemsetAsync(r, 0, cells * 8, st));
+      PPR_CUDA_TRY(cudaMemsetAsync(pi, 0, cells * 8, st));
+      PPR_CUDA_TRY(cudaMemsetAsync(counters, 0, 8 * (3 + 2 * KT), st));
+      PPR_CUDA_TRY(cudaMemcpyAsync(d_src, src_new, sizeof(src_new), cudaMemcpyHostToDevice, st));
+      uint32_t* fa = ws.front_a.as<uint32_t>();
+      uint32_t* fb = ws.front_b.as<uint32_t>();
+      const uint32_t epoch0 = ++g->stamp_epoch;
+      init_sources_kernel<KT><<<1, 32, 0, st>>>(d_src, ncols, r, ws.stamp.as<uint32_t>(), epoch0, fa);
+      ++launches;
+      uint64_t nfront = (uint64_t)ncols;
+      have_state = true;
+      while (true) {
+        PPR_CUDA_TRY(cudaMemsetAsync(counters, 0, 24, st));
+        PushArgs pa;
+        pa.front = fa;
+        pa.n_front = (uint32_t)nfront;
+        pa.out_rp = g->d_out_rp;
+        pa.out_ci = g->d_out_ci;
+        pa.deg = g->d_deg;
+        pa.r = r;
+        pa.pi = pi;
+        pa.stamp = ws.stamp.as<uint32_t>();
+        pa.next_stamp = ++g->stamp_epoch;
+        pa.next_front = fb;
+        pa.ent_share = ws.ent_share.as<u64>();
+        pa.ent_rem = ws.ent_rem.as<uint32_t>();
+        pa.chunks = ws.chunks.as<u64>();
+        pa.counters = counters;
+        pa.alpha64 = alpha64;
+        pa.rmax_raw = rmax_raw;
+        const int tb = (int)std::min<uint64_t>((nfront + 255) / 256, (uint64_t)grid_ew);
+        push_take_kernel<KT><<<std::max(tb, 1), 256, 0, st>>>(pa);
+        push_scatter_kernel<KT><<<grid_ew, 256, 0, st>>>(pa);
+        launches += 2;
+        PPR_CUDA_TRY(cudaGetLastError());
+        PPR_CUDA_TRY(cudaMemcpyAsync(hpin, counters, 8 * (3 + 2 * KT), cudaMemcpyDeviceToHost, st));
+        PPR_CUDA_TRY(cudaStreamSynchronize(st));
+        ++levels;
+        nfront = hpin[0];
+        const uint64_t fedges = hpin[1];
+        all_done = true;
+        for (int c = 0; c < ncols; ++c) {
+          u64 stopped = hpin[3 + c];
+          u64 rraw = kFixOneRaw - stopped;  // mass is conserved exactly: sum r = 1 - sum pi
+          rsum[c] = (double)rraw / kFixOne;
+          pushed[c] = (int64_t)hpin[3 + KT + c];
+          if (rraw > lambda_raw) all_done = false;
+        }
+        if (all_done || nfront == 0) break;
+        if ((int64_t)fedges > switch_edges) break;
+        if (levels > max_sweeps) { set_error("queue phase did not finish"); status = PPR_ERR_NOT_CONVERGED; break; }
+        std::swap(fa, fb);
+      }
+      if (status != PPR_OK) break;
+      for (int c = 0; c < KT; ++c) r0[c] = (1.0 - alpha) * rsum[c];
+    }
+    PPR_CUDA_TRY(cudaEventRecord(ev1, st));
+
+    // ---- sweep phase
+    int sweeps = 0;
+    std::vector<double> bound(KT, 0.0);
+    u64* xfinal = pi;  // the estimate to output
+    bool need_dense = !all_done;
+    if (!need_dense) {
+      for (int c = 0; c < ncols; ++c) bound[c] = rsum[c];
+    } else {
+      if (have_state) {
+        convert_kernel<KT><<<grid_ew, 256, 0, st>>>(n, r, pi, g->d_omega, alpha64, za);
+        ++launches;
+      } else {
+        PPR_CUDA_TRY(cudaMemsetAsync(za, 0, cells * 8, st));
+        for (int c = 0; c < KT; ++c) r0[c] = 1.0;
+      }
+      PPR_CUDA_TRY(cudaMemsetAsync(resid, 0, (size_t)(max_sweeps + 1) * 16 * 8, st));
+      SweepArgs sa;
+      sa.n = (int32_t)n;
+      sa.in_rp = g->d_in_rp;
+      sa.in_ci = g->d_in_ci;
+      sa.omega = g->d_omega;
+      sa.invw = g->d_invw;
+      sa.alpha_raw = alpha_raw;
+      for (int c = 0; c < 16; ++c) sa.src[c] = src_new[c];
+      sa.n_heavy = g->n_heavy;
+      sa.medium_end = plan.medium_end;
+      sa.n_pieces = g->n_pieces;
+      sa.piece_edges = g->piece_edges;
+      sa.piece_row = g->d_piece_row;
+      sa.piece_e0 = g->d_piece_e0;
+      sa.heavy_npieces = g->d_heavy_npieces;
+      sa.heavy_acc = ws.heavy_acc.as<u64>();
+      sa.heavy_cnt = ws.heavy_cnt.as<unsigned int>();
+      sa.nb_heavy = plan.nb_heavy;
+      sa.nb_medium = plan.nb_medium;
+      // x of the final pass goes to the residue buffer (free after the conversion)
+      u64* zcur = za;
+      u64* znext = zb;
+      double R = 0.0;
+      for (int c = 0; c < ncols; ++c) R = std::max(R, r0[c]);
+      while (true) {
+        int S = (R <= lambda) ? 1 : (int)std::ceil(std::log(lambda / R) / std::log(1.0 - alpha) - 1e-12);
+        S = std::max(S, 1);
+        if (sweeps + S > max_sweeps) {
+          set_error("sweep limit %d reached", max_sweeps);
+          status = PPR_ERR_NOT_CONVERGED;
+          break;
+        }
+        PPR_CUDA_TRY(cudaEventRecord(es0, st));
+        for (int j = 0; j < S; ++j) {
+          sa.z_in = zcur;
+          sa.z_out = znext;
+          sa.x_out = (j == S - 1) ? r : nullptr;
+          // after two passes rows without in-edges hold their constant value in
+          // both buffers; the pass that writes x still covers every row
+          sa.n = (sweeps + j >= 2 && !sa.x_out) ? n_nz : (int32_t)n;
+          sa.resid = resid + (size_t)(sweeps + j) * 16;
+          launch_sweep<KT>(sa, plan, st);
+          std::swap(zcur, znext);
+        }
+        PPR_CUDA_TRY(cudaEventRecord(es1, st));
+        PPR_CUDA_TRY(cudaGetLastError());
+        sweeps += S;
+        launches += S;
+        sweep_launches += S;
+        PPR_CUDA_TRY(cudaMemcpyAsync(hpin, resid + (size_t)(sweeps - 1) * 16, 16 * 8, cudaMemcpyDeviceToHost, st));
+        PPR_CUDA_TRY(cudaStreamSynchronize(st));
+        {
+          float a = 0.f;
+          cudaEventElapsedTime(&a, es0, es1);
+          ms_sweep += a;
+        }
+        const double* D = reinterpret_cast<const double*>(hpin);
+        // ||r(x_new)||_1 <= (1-alpha) ||r(x_old)||_1, with ||r(x_old)||_1 = ||x_new - x_old||_1 / alpha;
+        // the factor covers the float accumulation of the measurement, the
+        // additive term the fixed-point rounding of one pass (m half-ulps)
+        const double slack = (double)m * 0.5 / kFixOne / alpha;
+        bool ok = true;
+        R = 0.0;
+        for (int c = 0; c < ncols; ++c) {
+          double Dc = D[c] / kFixOne / alpha;
+          bound[c] = (1.0 - alpha) * Dc * (1.0 + 1e-4) + 2.0 * slack;
+          if (bound[c] > lambda) ok = false;
+          R = std::max(R, bound[c]);
+        }
+        if (ok) break;
+      }
+      if (status != PPR_OK) break;
+      xfinal = r;
+      if (out_r) {
+        // residual of the returned estimate: one more gather over z(x_final)
+        SweepArgs ra = sa;
+        const int ncols_i = ncols;
+        residual_kernel<KT><<<grid_ew, 256, 0, st>>>((int32_t)n, g->d_in_rp, g->d_in_ci, g->d_old_of_new, zcur, r,
+                                                     ra, ncols_i, t0, alpha, out_r_dev);
+        ++launches;
+      }
+    }
+    PPR_CUDA_TRY(cudaEventRecord(ev2, st));
+    PPR_CUDA_TRY(cudaMemsetAsync(counters + 64, 0, 8 * KT, st));
+    output_kernel<KT><<<grid_ew, 256, 0, st>>>(n, g->d_new_of_old, xfinal, ncols, t0, out_pi_dev, counters + 64);
+    ++launches;
+    if (!need_dense && out_r)  // the queue phase finished: its residue is the answer's residual
+      output_kernel<KT><<<grid_ew, 256, 0, st>>>(n, g->d_new_of_old, r, ncols, t0, out_r_dev, counters + 96), ++launches;
+    PPR_CUDA_TRY(cudaGetLastError());
+    PPR_CUDA_TRY(cudaMemcpyAsync(hpin, counters + 64, 8 * KT, cudaMemcpyDeviceToHost, st));
+    PPR_CUDA_TRY(cudaStreamSynchronize(st));
+    float a1 = 0, a2 = 0;
+    cudaEventElapsedTime(&a1, ev0, ev1);
+    cudaEventElapsedTime(&a2, ev0, ev2);
+    ms_push += a1;
+    ms_total += a2;
+    if (stats) {
+      for (int c = 0; c < ncols; ++c) {
+        ppr_stats& s = stats[t0 + c];
+        memset(&s, 0, sizeof(s));
+        s.sweeps = sweeps;
+        s.levels = levels;
+        s.edges_pushed = pushed[c];
+        s.edges_swept = (int64_t)sweeps * m;
+        s.initial_l1_residual = need_dense ? r0[c] : rsum[c];
+        s.final_l1_residual = bound[c];
+        s.mass_deficit = 1.0 - (double)hpin[c] / kFixOne;
+      }
+    }
+  }
+  if (status == PPR_OK) {
+    if (pi_on_host)
+      PPR_CUDA_TRY(cudaMemcpyAsync(out_pi, out_pi_dev, (size_t)k * n * 8, cudaMemcpyDeviceToHost, st));
+    if (r_on_host)
+      PPR_CUDA_TRY(cudaMemcpyAsync(out_r, out_r_dev, (size_t)k * n * 8, cudaMemcpyDeviceToHost, st));
+    PPR_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  if (stats && status == PPR_OK)
+    for (int32_t i = 0; i < k; ++i) {
+      stats[i].ms_push = ms_push;
+      stats[i].ms_sweep = ms_sweep;
+      stats[i].ms_total = ms_total;
+      stats[i].kernel_launches = launches;
+      stats[i].sweep_launches = sweep_launches;
+    }
+  for (cudaEvent_t e : {ev0, ev1, ev2, es0, es1}) cudaEventDestroy(e);
+  return status;
+}
+
+ppr_status query_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query_opts& o, double* out_pi,
+                    double* out_r, ppr_stats* stats, cudaStream_t st) {
+  int kt = o.k_tile;
+  if (kt == 0) kt = k >= 8 ? 8 : (k >= 4 ? 4 : (k >= 2 ? 2 : 1));
+  if ((size_t)g->n * kt >= ((size_t)1 << 32)) {
+    set_error("n * k_tile must stay below 2^32");
+    return PPR_ERR_ARG;
+  }
+  switch (kt) {
+    case 1: return run_hp<1>(g, src, k, o, out_pi, out_r, stats, st);
+    case 2: return run_hp<2>(g, src, k, o, out_pi, out_r, stats, st);
+    case 4: return run_hp<4>(g, src, k, o, out_pi, out_r, stats, st);
+    case 8: return run_hp<8>(g, src, k, o, out_pi, out_r, stats, st);
+    case 16: return run_hp<16>(g, src, k, o, out_pi, out_r, stats, st);
+    default: set_error("k_tile must be 0, 1, 2, 4, 8 or 16"); return PPR_ERR_ARG;
+  }
+}
+
+}  // namespace ppr

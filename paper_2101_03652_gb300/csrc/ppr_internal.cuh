@@ -1,0 +1,99 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ppr.h"
+
+namespace ppr {
+
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define PPR_CUDA_TRY(expr)                                                                        \
+  do {                                                                                            \
+    cudaError_t e_ = (expr);                                                                      \
+    if (e_ != cudaSuccess) {                                                                      \
+      ::ppr::set_error("CUDA error %s at %s:%d (%s)", cudaGetErrorString(e_), __FILE__, __LINE__, \
+                       #expr);                                                                    \
+      return e_ == cudaErrorMemoryAllocation ? PPR_ERR_OOM : PPR_ERR_CUDA;                        \
+    }                                                                                             \
+  } while (0)
+
+#define PPR_TRY(expr)                 \
+  do {                                \
+    ppr_status s_ = (expr);           \
+    if (s_ != PPR_OK) return s_;      \
+  } while (0)
+
+// Fixed-point format of the high-precision path: unsigned Q1.63, value = raw * 2^-63.
+constexpr double kFixOne = 9223372036854775808.0;  // 2^63
+constexpr uint64_t kFixOneRaw = 0x8000000000000000ull;
+
+// A device allocation that grows on demand and is reused across queries.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  ppr_status ensure(size_t want);
+  void release();
+  template <class T>
+  T* as() const { return static_cast<T*>(ptr); }
+};
+
+struct Workspace {
+  DevBuf r, pi, za, zb;          // n*KT uint64 each (HP): residue, reserve, ping-pong z
+  DevBuf stamp;                  // n*KT uint32 frontier membership stamps
+  DevBuf front_a, front_b;       // frontier lists (n*KT uint32)
+  DevBuf ent_share, ent_rem;     // per frontier entry: share and remainder of a push
+  DevBuf chunks;                 // edge-chunk records of a frontier level
+  DevBuf heavy_acc, heavy_cnt;   // partial sums of split rows
+  DevBuf counters;               // small device counters
+  DevBuf resid;                  // per-sweep per-column residual sums (double)
+  DevBuf stage;                  // device staging for host outputs
+  DevBuf walk_a, walk_b, walk_c; // APPROX path buffers
+  void* pinned = nullptr;        // small pinned host buffer for readbacks
+  size_t pinned_bytes = 0;
+  void release();
+};
+
+}  // namespace ppr
+
+struct ppr_graph {
+  int64_t n = 0, m = 0;
+  int device = -1;
+  // relabelling: nodes sorted by in-degree (descending, ties by original id)
+  std::vector<int32_t> h_new_of_old;   // new id of an original id
+  std::vector<int32_t> h_in_deg_sorted;  // in-degree of new id (non-increasing)
+  int32_t* d_new_of_old = nullptr;     // n
+  int32_t* d_old_of_new = nullptr;     // n
+  int32_t* d_out_rp = nullptr;         // n+1, out-CSR in new ids (original neighbour order)
+  int32_t* d_out_ci = nullptr;         // m
+  int32_t* d_in_rp = nullptr;          // n+1, in-CSR in new ids (rows ascending)
+  int32_t* d_in_ci = nullptr;          // m
+  int32_t* d_deg = nullptr;            // n, out-degree in new ids
+  // alpha-dependent per-node scale factors, cached for the last alpha used
+  double cached_alpha = -1.0;
+  uint64_t* d_omega = nullptr;         // round((1-alpha)/d * 2^64)
+  float* d_invw = nullptr;             // d / (1-alpha)
+  // heavy-row split for the pull sweep (rows with in-degree > heavy_deg)
+  int32_t heavy_deg = 0, piece_edges = 0;
+  int32_t n_heavy = 0, n_pieces = 0;
+  int32_t* d_piece_row = nullptr;
+  int32_t* d_piece_e0 = nullptr;
+  int32_t* d_heavy_npieces = nullptr;
+  uint32_t stamp_epoch = 0;
+  ppr::Workspace ws;
+};
+
+namespace ppr {
+ppr_status ensure_alpha(ppr_graph* g, double alpha, cudaStream_t st);
+ppr_status query_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query_opts& o, double* out_pi,
+                    double* out_r, ppr_stats* stats, cudaStream_t st);
+ppr_status query_approx(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query_opts& o, double* out_pi,
+                        double* out_r, uint32_t* out_counts, ppr_stats* stats, cudaStream_t st);
+bool is_device_pointer(const void* p);
+}  // namespace ppr

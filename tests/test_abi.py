@@ -1,0 +1,81 @@
+"""The C ABI library builds, loads and exports every declared symbol (no GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2101_03652_gb300 as P
+from paper_2101_03652_gb300 import binding
+import ppr_inputs as gen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(ppr_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = P.load_library()
+    names = declared_functions()
+    assert "ppr_graph_load" in names and "ppr_sssp_query" in names and "ppr_free" in names
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in binding.SIGNATURES, f"binding lacks {name}"
+
+
+def test_default_opts_and_struct_layout():
+    o = P.ppr_default_opts()
+    assert o.alpha == 0.2 and o.lambda_ == 1e-8 and o.eps == 0.5 and o.seed == 0x5EED
+    assert o.k_tile == 0 and o.epoch_num == 0 and o.switch_edges == -1 and o.max_sweeps == 0
+    # layout fixed by include/ppr.h (x86-64 and aarch64 LP64 agree)
+    assert ctypes.sizeof(binding.ppr_query_opts) == 72
+    assert ctypes.sizeof(binding.ppr_stats) == 112
+
+
+@pytest.mark.parametrize("case", ["sink", "self_loop", "unsorted", "out_of_range", "bad_rowptr"])
+def test_graph_contract_violations_rejected_before_device(case):
+    rp, ci = gen.fig1_graph()
+    rp = rp.copy()
+    ci = ci.copy()
+    if case == "sink":       # node 0 loses its out-edges
+        rp = np.array([0, 0, 4, 6, 9, 11], dtype=np.int64)
+        ci = ci[2:]
+    elif case == "self_loop":
+        ci[0] = 0
+    elif case == "unsorted":
+        ci[0], ci[1] = ci[1], ci[0]
+    elif case == "out_of_range":
+        ci[-1] = 5
+    elif case == "bad_rowptr":
+        rp[-1] += 1
+    with pytest.raises(P.PPRError) as e:
+        P.ppr_graph_load(rp, ci)
+    assert e.value.status == binding.PPR_ERR_GRAPH
+
+
+def test_null_and_empty_arguments():
+    lib = P.load_library()
+    h = ctypes.c_void_p()
+    assert lib.ppr_graph_load(None, None, 5, 13, None, ctypes.byref(h)) == binding.PPR_ERR_ARG
+    assert lib.ppr_sssp_query(None, None, 0, 0, None, None, None, None, None, None) == binding.PPR_ERR_ARG
+    lib.ppr_free(None)  # NULL-safe
+    assert lib.ppr_graph_n(None) == 0
+
+
+def test_no_cpu_fallback_without_device():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    rp, ci = gen.fig1_graph()
+    with pytest.raises(P.PPRError) as e:
+        P.ppr_graph_load(rp, ci)
+    assert e.value.status == binding.PPR_ERR_CUDA

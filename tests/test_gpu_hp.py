@@ -1,0 +1,185 @@
+"""High-precision queries on the GPU (C ABI) against the FP64 oracle.
+
+Bar: l1 distance to the oracle <= 2 lambda per source (both are within
+lambda of the exact vector), certified bound <= lambda, exact agreement with
+PowItr when every pass pushes every node (Lemma 1), and the mass identity
+sum(pi_hat) = 1 - ||r||_1 for zero starts.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import ppr_inputs as gen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+LAM = 1e-8
+ALPHA = 0.2
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2101_03652_gb300 as P
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    P.load_library()
+    return P
+
+
+@pytest.fixture(scope="module")
+def c0():
+    rp, ci = gen.chung_lu(10_000, 100_000, 2.2, seed=1)
+    return rp, ci, gen.sources(10_000, 10, seed=1)
+
+
+@pytest.fixture(scope="module")
+def c0_ref(c0):
+    rp, ci, src = c0
+    og = O.Graph(rp, ci)
+    return {int(s): O.powerpush(og, int(s), ALPHA, LAM)[0] for s in src}
+
+
+def run(P, rp, ci, src, **kw):
+    g = P.Graph(rp, ci)
+    out_r = kw.pop("out_r", None)
+    pi, st = g.query(np.asarray(src), P.PPR_HP, out_r=out_r, lam=kw.pop("lam", LAM), **kw)
+    torch.cuda.synchronize()
+    res = pi.cpu().numpy()
+    g.close()
+    return res, st
+
+
+def check_bound_and_mass(st, lam=LAM):
+    for s in st:
+        assert s["final_l1_residual"] <= lam
+        assert -1e-15 <= s["mass_deficit"] <= s["final_l1_residual"] + 1e-15
+
+
+@pytest.mark.parametrize("k_tile", [1, 2, 4, 8])
+def test_c0_chung_lu_against_powerpush(P, c0, c0_ref, k_tile):
+    rp, ci, src = c0
+    pi, st = run(P, rp, ci, src, k_tile=k_tile)
+    for i, s in enumerate(src):
+        assert np.abs(pi[i] - c0_ref[int(s)]).sum() <= 2 * LAM
+    check_bound_and_mass(st)
+    assert all(x["sweeps"] == st[0]["sweeps"] for x in st[: min(k_tile, len(st))])
+
+
+def test_lemma1_sweeps_equal_powitr(P, c0):
+    """With no queue phase every pass is one SimFwdPush iteration: 83 passes
+    for lambda = 1e-8, alpha = 0.2, equal to PowItr up to summation order."""
+    rp, ci, src = c0
+    og = O.Graph(rp, ci)
+    pi, st = run(P, rp, ci, src[:3], k_tile=4, switch_edges=0)
+    for i, s in enumerate(src[:3]):
+        ref, _, ost = O.powitr(og, int(s), ALPHA, LAM)
+        assert ost["iterations"] == 83 and st[i]["sweeps"] == 83
+        assert np.abs(pi[i] - ref).sum() <= 1e-13
+    check_bound_and_mass(st)
+
+
+def test_subgraph200_against_dense_solve(P, c0):
+    rp, ci, _ = c0
+    srp, sci = gen.bfs_subgraph(rp, ci, 0, 200, seed=1)
+    og = O.Graph(srp, sci)
+    src = np.arange(0, 200, 13, dtype=np.int32)
+    pi, st = run(P, srp, sci, src)
+    for i, s in enumerate(src):
+        assert np.abs(pi[i] - O.dense_solve(og, int(s), ALPHA)).sum() <= LAM
+    check_bound_and_mass(st)
+
+
+def test_fig1_and_two_node_graphs(P):
+    rp, ci = gen.fig1_graph()
+    og = O.Graph(rp, ci)
+    src = np.array([0, 1, 2, 3, 4, 0], dtype=np.int32)
+    pi, st = run(P, rp, ci, src)
+    for i, s in enumerate(src):
+        assert np.abs(pi[i] - O.dense_solve(og, int(s), ALPHA)).sum() <= LAM
+    rp2, ci2 = gen.from_edges(2, [(0, 1), (1, 0)])
+    pi2, _ = run(P, rp2, ci2, [1])
+    # pi(1,1) = alpha / (1 - (1-alpha)^2), pi(1,0) = (1-alpha) pi(1,1)
+    p11 = ALPHA / (1 - (1 - ALPHA) ** 2)
+    assert np.abs(pi2[0] - np.array([(1 - ALPHA) * p11, p11])).sum() <= LAM
+
+
+def test_duplicates_and_ragged_tile(P, c0, c0_ref):
+    rp, ci, src = c0
+    dup = np.array([src[0], src[1], src[0], src[2], src[0]], dtype=np.int32)
+    pi, st = run(P, rp, ci, dup, k_tile=4)
+    for i, s in enumerate(dup):
+        assert np.abs(pi[i] - c0_ref[int(s)]).sum() <= 2 * LAM
+
+
+def test_queue_phase_alone_and_loose_lambda(P, c0):
+    """A loose lambda is reached inside the queue phase (no sweep)."""
+    rp, ci, src = c0
+    og = O.Graph(rp, ci)
+    lam = 1e-2
+    pi, st = run(P, rp, ci, src[:4], lam=lam, switch_edges=10**12)
+    for i, s in enumerate(src[:4]):
+        assert st[i]["sweeps"] == 0
+        ref, _, _ = O.powitr(og, int(s), ALPHA, 1e-12)
+        assert np.abs(pi[i] - ref).sum() <= lam
+    check_bound_and_mass(st, lam)
+
+
+def test_returned_residual_matches_definition(P, c0):
+    """out_r = (alpha e_s + (1-alpha) pi_hat P - pi_hat) / alpha of the returned
+    pi_hat, recomputed by the oracle; its l1 norm is within the certified bound."""
+    rp, ci, src = c0
+    og = O.Graph(rp, ci)
+    k = 3
+    out_r = torch.empty((k, len(rp) - 1), dtype=torch.float64, device="cuda")
+    pi, st = run(P, rp, ci, src[:k], out_r=out_r)
+    r = out_r.cpu().numpy()
+    for i, s in enumerate(src[:k]):
+        ref = O.residual(og, int(s), pi[i], ALPHA)
+        assert np.abs(r[i] - ref).max() <= 1e-15 + 1e-9 * np.abs(ref).max()
+        assert np.abs(r[i]).sum() <= st[i]["final_l1_residual"]
+        assert abs(r[i].sum() - st[i]["mass_deficit"]) <= 1e-12
+
+
+def test_host_output_buffers(P, c0, c0_ref):
+    rp, ci, src = c0
+    g = P.Graph(rp, ci)
+    out = np.zeros((3, len(rp) - 1))
+    out_r = np.zeros((3, len(rp) - 1))
+    _, st = g.query(src[:3], P.PPR_HP, out_pi=out, out_r=out_r, lam=LAM)
+    g.close()
+    for i, s in enumerate(src[:3]):
+        assert np.abs(out[i] - c0_ref[int(s)]).sum() <= 2 * LAM
+        assert np.abs(out_r[i]).sum() <= st[i]["final_l1_residual"]
+
+
+def test_argument_errors(P, c0):
+    rp, ci, src = c0
+    g = P.Graph(rp, ci)
+    for bad in ([-1], [10_000]):
+        with pytest.raises(P.PPRError):
+            g.query(bad, P.PPR_HP)
+    for kw in ({"lam": 0.0}, {"alpha": 1.0}, {"alpha": 0.0}, {"k_tile": 3}, {"max_sweeps": 5}):
+        with pytest.raises(P.PPRError):
+            g.query(src[:2], P.PPR_HP, **kw)
+    g.close()
+
+
+@pytest.fixture(scope="module")
+def rmat20():
+    rp, ci = gen.rmat(20, 16, seed=1)
+    return rp, ci, gen.sources(len(rp) - 1, 64, seed=2)
+
+
+def test_rmat20_bench_configuration(P, rmat20):
+    """The benchmark's launch: 64 sources, k_tile 8.  Two sampled sources are
+    checked against the oracle in full; every source satisfies the certified
+    bound and the mass identity."""
+    rp, ci, src = rmat20
+    pi, st = run(P, rp, ci, src, k_tile=8)
+    check_bound_and_mass(st)
+    og = O.Graph(rp, ci)
+    for i in (0, 37):
+        ref, _, _ = O.powerpush(og, int(src[i]), ALPHA, LAM)
+        assert np.abs(pi[i] - ref).sum() <= 2 * LAM
+    assert np.all(pi >= 0)
