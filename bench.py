@@ -32,7 +32,8 @@ sys.path.insert(0, ROOT)
 
 WORKLOADS = {
     # name: (scale, edge_factor, k per step, k_tile)
-    "rmat20-k64": (20, 16, 64, 8),
+    "rmat20-k64": (20, 16, 64, 64),
+    "rmat20-k16": (20, 16, 16, 16),
     "rmat20-k8": (20, 16, 8, 8),
     "rmat22-k1": (22, 16, 1, 1),
 }
@@ -118,7 +119,7 @@ def ncu_traffic(workload: str):
     try:
         with open(path) as f:
             rec = json.load(f)
-        if rec.get("kernel_source_sha") == kernel_source_sha() and rec.get("workload") == workload:
+        if rec.get("kernel_source_sha") == kernel_source_sha() and workload in rec.get("workloads", []):
             return float(rec["dram_bytes_per_launch"])
     except Exception:
         pass

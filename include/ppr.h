@@ -53,7 +53,7 @@ typedef struct {
   double eps;              /* APPROX relative error, > 0 */
   double mu;               /* APPROX value threshold; 0 means 1/n */
   uint64_t seed;           /* APPROX: Philox-4x32-10 key for the walks */
-  int32_t k_tile;          /* sources solved together per pass: 1,2,4,8; 0 = auto */
+  int32_t k_tile;          /* sources solved together per pass: 1,2,4,...,64; 0 = auto */
   int32_t epoch_num;       /* dense phase: 0 = push every node each sweep (SimFwdPush,
                               Sec. 4.1); >0 = Algorithm 3's epochs with thresholds
                               lambda^(i/epoch_num)/m */

@@ -139,6 +139,10 @@ static void free_graph_arrays(ppr_graph* g) {
                   (void*)g->d_in_rp, (void*)g->d_in_ci, (void*)g->d_deg, (void*)g->d_omega, (void*)g->d_invw,
                   (void*)g->d_piece_row, (void*)g->d_piece_e0, (void*)g->d_heavy_npieces})
     if (p) cudaFree(p);
+  for (auto& pl : g->plans) {
+    if (pl.d_items) cudaFree(pl.d_items);
+    if (pl.d_npieces) cudaFree(pl.d_npieces);
+  }
 }
 
 static ppr_status build_and_upload(ppr_graph* g, const int64_t* rp, const int32_t* ci, cudaStream_t st) {

@@ -195,8 +195,10 @@ __global__ void convert_kernel(int64_t n, const u64* __restrict__ r, const u64* 
 
 // ------------------------------------------------------------ sweep phase
 struct SweepArgs {
-  int32_t n;         // rows processed: all rows, or only rows with in-degree > 0 once
-                     // the others hold their final (constant) value in both buffers
+  int32_t n_items;   // work items of this pass (items over rows without in-edges come last and
+                     // are left out once those rows hold their constant value in both buffers)
+  const int4* items; // {kind, a, b, c}: kind 0 = piece [b, c) of split row a; 1 = rows [a, b)
+                     // one warp per row; 2 = rows [a, b) with L lanes per row
   const int32_t* in_rp;
   const int32_t* in_ci;
   const uint64_t* omega;
@@ -204,18 +206,17 @@ struct SweepArgs {
   const u64* z_in;
   u64* z_out;
   u64* x_out;        // optional: the estimate x of this pass
-  int32_t src[16];   // tile's sources (new ids), -1 for unused columns
+  int32_t src[64];   // tile's sources (new ids), -1 for unused columns
   u64 alpha_raw;     // alpha in Q1.63
   double* resid;     // [KT] sums of |x_new - x_old| in raw units (this pass)
-  int32_t n_heavy, medium_end;
-  int32_t n_pieces, piece_edges;
-  const int32_t* piece_row;
-  const int32_t* piece_e0;
   const int32_t* heavy_npieces;
   u64* heavy_acc;
   unsigned int* heavy_cnt;
-  int32_t nb_heavy, nb_medium;
 };
+
+constexpr int kItemPeriods = 16;  // target cost of one work item (see build_plan)
+constexpr int kLightMax = 16;     // rows with at most this many in-edges use lane groups
+constexpr int kUnr = 4;           // gathers each lane issues before consuming them
 
 template <int KT>
 struct Lay {
@@ -297,25 +298,27 @@ __device__ __forceinline__ void gather_warp(const SweepArgs& a, int e_begin, int
 }
 
 template <int KT>
-__global__ void __launch_bounds__(256, 4) sweep_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(256, 6) sweep_kernel(SweepArgs a) {
   constexpr int V = Lay<KT>::V, L = Lay<KT>::L;
-  constexpr int UNR = 4;
+  constexpr int UNR = kUnr;
   const int lane = threadIdx.x & 31;
   const int slot = lane % L;
   float res[V];
 #pragma unroll
   for (int q = 0; q < V; ++q) res[q] = 0.f;
 
-  if ((int)blockIdx.x < a.nb_heavy) {
-    // split rows: one warp per piece, partial sums combined with integer atomics;
-    // the last piece of a row to arrive finishes it
-    const int nw = a.nb_heavy * (blockDim.x >> 5);
-    for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < a.n_pieces; p += nw) {
-      const int u = a.piece_row[p];
-      const int e0 = a.piece_e0[p];
-      const int e1 = min(e0 + a.piece_edges, __ldg(&a.in_rp[u + 1]));
+  // Items are about equally long and grouped by kind; dealing them to warps
+  // round-robin gives every warp nearly the same amount and mix of work
+  // without any atomic on the claim path.
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < a.n_items; it += nwarps) {
+    const int4 w = __ldg(&a.items[it]);
+    if (w.x == 0) {
+      // piece of a split row: partial sums combined with integer atomics; the
+      // last piece of the row to arrive finishes it
+      const int u = w.y;
       u64 acc[V] = {};
-      gather_warp<KT, UNR>(a, e0, e1, lane, slot, acc);
+      gather_warp<KT, UNR>(a, w.z, w.w, lane, slot, acc);
 #pragma unroll
       for (int off = L; off < 32; off <<= 1)
 #pragma unroll
@@ -337,59 +340,37 @@ __global__ void __launch_bounds__(256, 4) sweep_kernel(SweepArgs a) {
         }
         if (lane == 0) atomicExch(&a.heavy_cnt[u], 0u);
       }
-    }
-  } else if ((int)blockIdx.x < a.nb_heavy + a.nb_medium) {
-    // medium rows: one warp per row
-    const int nw = a.nb_medium * (blockDim.x >> 5);
-    const int w0 = ((blockIdx.x - a.nb_heavy) * blockDim.x + threadIdx.x) >> 5;
-    for (int u = a.n_heavy + w0; u < a.medium_end; u += nw) {
-      u64 acc[V] = {};
-      gather_warp<KT, UNR>(a, __ldg(&a.in_rp[u]), __ldg(&a.in_rp[u + 1]), lane, slot, acc);
+    } else if (w.x == 1) {
+      // medium rows: one warp per row
+      for (int u = w.y; u < w.z; ++u) {
+        u64 acc[V] = {};
+        gather_warp<KT, UNR>(a, __ldg(&a.in_rp[u]), __ldg(&a.in_rp[u + 1]), lane, slot, acc);
 #pragma unroll
-      for (int off = L; off < 32; off <<= 1)
+        for (int off = L; off < 32; off <<= 1)
 #pragma unroll
-        for (int q = 0; q < V; ++q) acc[q] += __shfl_xor_sync(kFull, acc[q], off);
-      if (lane < L) row_epilogue<KT>(a, u, slot, acc, res);
-    }
-  } else {
-    // light rows: L lanes per row, 32/L consecutive rows per warp; the trip
-    // count is the warp's largest row (rows are sorted by length, so the
-    // rows of one warp have nearly equal length)
-    constexpr int RPW = 32 / L;
-    const int nwl = (gridDim.x - a.nb_heavy - a.nb_medium) * (blockDim.x >> 5);
-    const int wl = ((blockIdx.x - a.nb_heavy - a.nb_medium) * blockDim.x + threadIdx.x) >> 5;
-    for (int row0 = a.medium_end + wl * RPW; row0 < a.n; row0 += nwl * RPW) {
-      const int u = row0 + lane / L;
-      const bool live = u < a.n;
-      const int e0 = live ? __ldg(&a.in_rp[u]) : 0;
-      const int d = live ? __ldg(&a.in_rp[u + 1]) - e0 : 0;
-      const int dmax = __reduce_max_sync(kFull, d);
-      u64 acc[V] = {};
-      for (int j = 0; j < dmax; j += UNR) {
-        int v[UNR];
-#pragma unroll
-        for (int q = 0; q < UNR; ++q) v[q] = (j + q < d) ? __ldg(&a.in_ci[e0 + j + q]) : -1;
-        u64 t[UNR][V];
-#pragma unroll
-        for (int q = 0; q < UNR; ++q) {
-          if (v[q] >= 0) {
-            ld_vec<V>(a.z_in + (size_t)v[q] * KT + slot * V, t[q]);
-          } else {
-#pragma unroll
-            for (int w = 0; w < V; ++w) t[q][w] = 0;
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < UNR; ++q)
-#pragma unroll
-          for (int w = 0; w < V; ++w) acc[w] += t[q][w];
+          for (int q = 0; q < V; ++q) acc[q] += __shfl_xor_sync(kFull, acc[q], off);
+        if (lane < L) row_epilogue<KT>(a, u, slot, acc, res);
       }
-      if (live) row_epilogue<KT>(a, u, slot, acc, res);
+    } else {
+      // light rows: L lanes per row, 32/L consecutive rows at a time (rows are
+      // sorted by length, so rows sharing a warp have nearly equal length)
+      for (int u = w.y + lane / L; u < w.z; u += 32 / L) {
+        const int e1 = __ldg(&a.in_rp[u + 1]);
+        u64 acc[V] = {};
+#pragma unroll 4
+        for (int e = __ldg(&a.in_rp[u]); e < e1; ++e) {
+          u64 t[V];
+          ld_vec<V>(a.z_in + (size_t)__ldg(&a.in_ci[e]) * KT + slot * V, t);
+#pragma unroll
+          for (int q = 0; q < V; ++q) acc[q] += t[q];
+        }
+        row_epilogue<KT>(a, u, slot, acc, res);
+      }
     }
   }
 
   // per-column residual: lanes with equal slot, then warps, then one atomic per column
-  __shared__ float sred[8][16];
+  __shared__ float sred[8][KT];
 #pragma unroll
   for (int off = L; off < 32; off <<= 1)
 #pragma unroll
@@ -406,31 +387,30 @@ __global__ void __launch_bounds__(256, 4) sweep_kernel(SweepArgs a) {
   }
 }
 
-// out[(col0 + c) * n + o] = x[new(o)][c] as float64; exact per-column sums of x
+// out[(col0 + c) * n + o] = x[new(o)][c] as float64 (writes coalesced along o)
 template <int KT>
 __global__ void output_kernel(int64_t n, const int32_t* __restrict__ new_of_old, const u64* __restrict__ x,
-                              int ncols, int64_t col0, double* __restrict__ out, u64* mass) {
-  u64 ms[KT];
-#pragma unroll
-  for (int c = 0; c < KT; ++c) ms[c] = 0;
+                              int ncols, int64_t col0, double* __restrict__ out) {
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
     const int64_t u = new_of_old[o];
-#pragma unroll
-    for (int c = 0; c < KT; ++c) {
-      if (c < ncols) {
-        u64 v = x[u * KT + c];
-        ms[c] += v;
-        out[(col0 + c) * n + o] = (double)v * (1.0 / kFixOne);
-      }
-    }
+    for (int c = 0; c < ncols; ++c) out[(col0 + c) * n + o] = (double)x[u * KT + c] * (1.0 / kFixOne);
   }
-#pragma unroll
-  for (int c = 0; c < KT; ++c) {
-    u64 s = ms[c];
-#pragma unroll
-    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
-    if ((threadIdx.x & 31) == 0 && c < ncols) atomicAdd(&mass[c], s);
-  }
+}
+
+// exact per-column sums of a tile (integer adds; the block size is a multiple
+// of KT, so each thread always reads the same column)
+template <int KT>
+__global__ void column_sum_kernel(int64_t n, const u64* __restrict__ x, u64* __restrict__ mass) {
+  __shared__ u64 part[KT];
+  if (threadIdx.x < KT) part[threadIdx.x] = 0;
+  __syncthreads();
+  u64 acc = 0;
+  const int64_t total = n * KT;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    acc += x[i];
+  atomicAdd(&part[threadIdx.x % KT], acc);
+  __syncthreads();
+  if (threadIdx.x < KT) atomicAdd(&mass[threadIdx.x], part[threadIdx.x]);
 }
 
 // push residual of the returned estimate: r = (alpha e_s + sum z(v) - x(u)) / alpha
@@ -468,47 +448,75 @@ static int sm_count() {
   return cached;
 }
 
-struct Plan {
-  int kt;
-  int32_t medium_end;
-  int nb_heavy, nb_medium, nb_light;
-};
+// Work list of one pass for a tile width.  Costs are counted in "periods":
+// one round of UNR dependent gathers by a warp (or by a lane group for light
+// rows).  Rows longer than one piece are split into pieces; other rows are
+// grouped so that every item costs about kItemPeriods periods.  Items are
+// ordered split pieces, medium rows, light rows, rows without in-edges.
+using Plan = ppr_graph::SweepPlan;
 
-static Plan make_plan(const ppr_graph* g, int kt, int blocks_per_sm) {
-  Plan p;
-  p.kt = kt;
-  const int light_max = 16;
-  // rows [n_heavy, medium_end) have in-degree in (light_max, heavy_deg]
+static ppr_status build_plan(ppr_graph* g, int kt, Plan& p, cudaStream_t st) {
   const std::vector<int32_t>& d = g->h_in_deg_sorted;
-  int32_t lo = g->n_heavy, hi = (int32_t)g->n;
-  while (lo < hi) {
-    int32_t mid = lo + (hi - lo) / 2;
-    if (d[mid] > light_max) lo = mid + 1; else hi = mid;
+  const int32_t n = (int32_t)g->n;
+  const int L = kt >= 2 ? kt / 2 : 1;
+  const int epw = 32 / L;                 // edges per warp step
+  const int piece = std::max(kItemPeriods * epw * kUnr, 256);  // wide tiles: keep split rows few
+  const int rpw = 32 / L;                 // light rows per warp
+  std::vector<int4> items;
+  std::vector<int32_t> npieces;
+  int64_t e = 0;
+  int32_t u = 0;
+  for (; u < n && d[u] > piece; ++u) {
+    int np = 0;
+    for (int64_t b = e; b < e + d[u]; b += piece, ++np)
+      items.push_back(make_int4(0, u, (int)b, (int)std::min<int64_t>(b + piece, e + d[u])));
+    npieces.push_back(np);
+    e += d[u];
   }
-  p.medium_end = lo;
-  // split a persistent-size grid by estimated work (edges, plus a row overhead)
-  double e_heavy = 0, e_med = 0, e_light = 0;
-  for (int32_t u = 0; u < g->n_heavy; ++u) e_heavy += d[u];
-  for (int32_t u = g->n_heavy; u < p.medium_end; ++u) e_med += d[u] + 8;
-  for (int32_t u = p.medium_end; u < (int32_t)g->n; ++u) e_light += d[u] + 2;
-  const int total = sm_count() * blocks_per_sm;  // every block resident at once
-  double sum = e_heavy + e_med + e_light;
-  p.nb_heavy = g->n_pieces > 0 ? std::max(1, (int)std::lround(total * e_heavy / sum)) : 0;
-  p.nb_medium = p.medium_end > g->n_heavy ? std::max(1, (int)std::lround(total * e_med / sum)) : 0;
-  p.nb_light = std::max(1, total - p.nb_heavy - p.nb_medium);
-  return p;
+  const int32_t n_split = u;
+  while (u < n && d[u] > kLightMax) {
+    int32_t u0 = u;
+    int cost = 0;
+    while (u < n && d[u] > kLightMax) {
+      int c = (d[u] + epw * kUnr - 1) / (epw * kUnr) + 1;
+      if (cost > 0 && cost + c > kItemPeriods) break;
+      cost += c;
+      ++u;
+    }
+    items.push_back(make_int4(1, u0, u, 0));
+  }
+  while (u < n && d[u] > 0) {
+    int32_t u0 = u;
+    int cost = 0;
+    while (u < n && d[u] > 0) {
+      int c = (d[u] + kUnr - 1) / kUnr + 1;  // the block's first row is its longest
+      if (cost > 0 && cost + c > kItemPeriods) break;
+      cost += c;
+      for (int r = 0; r < rpw && u < n && d[u] > 0; ++r) ++u;
+    }
+    items.push_back(make_int4(2, u0, u, 0));
+  }
+  p.n_items_nz = (int32_t)items.size();
+  while (u < n) {
+    int32_t u0 = u;
+    u = (int32_t)std::min<int64_t>(n, (int64_t)u + (int64_t)kItemPeriods * rpw);
+    items.push_back(make_int4(2, u0, u, 0));
+  }
+  p.n_items_all = (int32_t)items.size();
+  p.n_split = n_split;
+  p.kt = kt;
+  PPR_CUDA_TRY(cudaMalloc((void**)&p.d_items, sizeof(int4) * std::max<size_t>(items.size(), 1)));
+  PPR_CUDA_TRY(cudaMemcpyAsync(p.d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st));
+  PPR_CUDA_TRY(cudaMalloc((void**)&p.d_npieces, sizeof(int32_t) * std::max<size_t>(npieces.size(), 1)));
+  PPR_CUDA_TRY(cudaMemcpyAsync(p.d_npieces, npieces.data(), sizeof(int32_t) * npieces.size(),
+                               cudaMemcpyHostToDevice, st));
+  PPR_CUDA_TRY(cudaStreamSynchronize(st));
+  return PPR_OK;
 }
 
 template <int KT>
-static void launch_sweep(const SweepArgs& a, const Plan& p, cudaStream_t st) {
-  static bool configured = false;
-  if (!configured) {
-    // the kernel needs almost no shared memory: give the SM's storage to L1,
-    // which caches the gathered rows of the most-referenced nodes
-    cudaFuncSetAttribute(sweep_kernel<KT>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-    configured = true;
-  }
-  sweep_kernel<KT><<<p.nb_heavy + p.nb_medium + p.nb_light, 256, 0, st>>>(a);
+static void launch_sweep(const SweepArgs& a, int grid, cudaStream_t st) {
+  sweep_kernel<KT><<<grid, 256, 0, st>>>(a);
 }
 
 template <int KT>
@@ -524,7 +532,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
                                           : 4 * (int)std::ceil(std::log(lambda) / std::log(1.0 - alpha)) + 64;
 
   // admission: state for one tile plus staging of host outputs
-  size_t need = 4 * cells * 8 + cells * 4 * 4 + cells * 16 + (size_t)m * KT / kPushChunk * 8 + (size_t)g->n_heavy * KT * 8 + (size_t)max_sweeps * KT * 8;
+  size_t need = 4 * cells * 8 + cells * 4 * 4 + cells * 16 + (size_t)m * KT / kPushChunk * 8 + (size_t)max_sweeps * KT * 8;
   size_t stage_bytes = 0;
   if (pi_on_host) stage_bytes += (size_t)k * n * 8;
   if (r_on_host) stage_bytes += (size_t)k * n * 8;
@@ -549,11 +557,19 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
   PPR_TRY(ws.ent_share.ensure(cells * 8));
   PPR_TRY(ws.ent_rem.ensure(cells * 4));
   PPR_TRY(ws.chunks.ensure((cells + (size_t)m * KT / kPushChunk + 64) * 8));
-  bool fresh_heavy = ws.heavy_acc.ptr == nullptr || ws.heavy_cnt.ptr == nullptr;
-  PPR_TRY(ws.heavy_acc.ensure(std::max<size_t>((size_t)g->n_heavy * 16 * 8, 8)));
-  PPR_TRY(ws.heavy_cnt.ensure(std::max<size_t>((size_t)g->n_heavy * 4, 4)));
-  PPR_TRY(ws.counters.ensure(4096));
-  PPR_TRY(ws.resid.ensure((size_t)(max_sweeps + 1) * 16 * 8));
+  static_assert(KT >= 1 && KT <= 64 && (KT & (KT - 1)) == 0, "tile width must be a power of two <= 64");
+  int plan_slot = 0;
+  while ((1 << plan_slot) < KT) ++plan_slot;
+  Plan& plan = g->plans[plan_slot];
+  if (plan.kt != KT) PPR_TRY(build_plan(g, KT, plan, st));
+  const size_t acc_bytes = std::max<size_t>((size_t)plan.n_split * KT * 8, 8);
+  const size_t cnt_bytes = std::max<size_t>((size_t)plan.n_split * 4, 4);
+  bool fresh_heavy = ws.heavy_acc.bytes < acc_bytes || ws.heavy_cnt.bytes < cnt_bytes;
+  PPR_TRY(ws.heavy_acc.ensure(acc_bytes));
+  PPR_TRY(ws.heavy_cnt.ensure(cnt_bytes));
+  PPR_TRY(ws.counters.ensure(8192));
+  PPR_TRY(ws.resid.ensure((size_t)(max_sweeps + 1) * 64 * 8));
+
   if (stage_bytes) PPR_TRY(ws.stage.ensure(stage_bytes));
   if (!ws.pinned) {
     PPR_CUDA_TRY(cudaMallocHost(&ws.pinned, 65536));
@@ -576,7 +592,8 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
   u64* counters = ws.counters.as<u64>();
   double* resid = ws.resid.as<double>();
   u64* hpin = static_cast<u64*>(ws.pinned);
-  int32_t* d_src = reinterpret_cast<int32_t*>(counters + 256);  // device copy of the tile's sources
+  int32_t* d_src = reinterpret_cast<int32_t*>(counters + 512);  // device copy of the tile's sources
+  u64* mass = counters + 256;                                    // exact column sums of the output
   double* out_pi_dev = pi_on_host ? ws.stage.as<double>() : out_pi;
   double* out_r_dev = !out_r ? nullptr : (r_on_host ? ws.stage.as<double>() + (pi_on_host ? (size_t)k * n : 0) : out_r);
 
@@ -588,7 +605,8 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
   const int64_t switch_edges = o.switch_edges >= 0 ? o.switch_edges : (int64_t)(0.02 * (double)m * KT);
   int bps = 0;
   PPR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, sweep_kernel<KT>, 256, 0));
-  const Plan plan = make_plan(g, KT, std::max(bps, 1));
+  const int sweep_grid = sm_count() * std::max(bps, 1);
+
   const int grid_ew = sm_count() * 8;
 
   cudaEvent_t ev0, ev1, ev2, es0, es1;
@@ -599,22 +617,13 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
   PPR_CUDA_TRY(cudaEventCreate(&es1));
   float ms_push = 0.f, ms_sweep = 0.f, ms_total = 0.f;
   int64_t launches = 0, sweep_launches = 0;
-  int32_t n_nz = 0;  // rows with in-degree > 0 are the first n_nz rows
-  {
-    const std::vector<int32_t>& d = g->h_in_deg_sorted;
-    int32_t lo = 0, hi = (int32_t)n;
-    while (lo < hi) {
-      int32_t mid = lo + (hi - lo) / 2;
-      if (d[mid] > 0) lo = mid + 1; else hi = mid;
-    }
-    n_nz = lo;
-  }
+
   ppr_status status = PPR_OK;
 
   for (int32_t t0 = 0; t0 < k && status == PPR_OK; t0 += KT) {
     const int ncols = std::min<int32_t>(KT, k - t0);
-    int32_t src_new[16];
-    for (int c = 0; c < 16; ++c) src_new[c] = c < ncols ? g->h_new_of_old[src[t0 + c]] : -1;
+    int32_t src_new[64];
+    for (int c = 0; c < 64; ++c) src_new[c] = c < ncols ? g->h_new_of_old[src[t0 + c]] : -1;
     PPR_CUDA_TRY(cudaEventRecord(ev0, st));
 
     // ---- queue phase
@@ -631,7 +640,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
       uint32_t* fa = ws.front_a.as<uint32_t>();
       uint32_t* fb = ws.front_b.as<uint32_t>();
       const uint32_t epoch0 = ++g->stamp_epoch;
-      init_sources_kernel<KT><<<1, 32, 0, st>>>(d_src, ncols, r, ws.stamp.as<uint32_t>(), epoch0, fa);
+      init_sources_kernel<KT><<<1, 64, 0, st>>>(d_src, ncols, r, ws.stamp.as<uint32_t>(), epoch0, fa);
       ++launches;
       uint64_t nfront = (uint64_t)ncols;
       have_state = true;
@@ -697,26 +706,19 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
         PPR_CUDA_TRY(cudaMemsetAsync(za, 0, cells * 8, st));
         for (int c = 0; c < KT; ++c) r0[c] = 1.0;
       }
-      PPR_CUDA_TRY(cudaMemsetAsync(resid, 0, (size_t)(max_sweeps + 1) * 16 * 8, st));
+      PPR_CUDA_TRY(cudaMemsetAsync(resid, 0, (size_t)(max_sweeps + 1) * 64 * 8, st));
+
       SweepArgs sa;
-      sa.n = (int32_t)n;
+      sa.items = plan.d_items;
       sa.in_rp = g->d_in_rp;
       sa.in_ci = g->d_in_ci;
       sa.omega = g->d_omega;
       sa.invw = g->d_invw;
       sa.alpha_raw = alpha_raw;
-      for (int c = 0; c < 16; ++c) sa.src[c] = src_new[c];
-      sa.n_heavy = g->n_heavy;
-      sa.medium_end = plan.medium_end;
-      sa.n_pieces = g->n_pieces;
-      sa.piece_edges = g->piece_edges;
-      sa.piece_row = g->d_piece_row;
-      sa.piece_e0 = g->d_piece_e0;
-      sa.heavy_npieces = g->d_heavy_npieces;
+      for (int c = 0; c < 64; ++c) sa.src[c] = src_new[c];
+      sa.heavy_npieces = plan.d_npieces;
       sa.heavy_acc = ws.heavy_acc.as<u64>();
       sa.heavy_cnt = ws.heavy_cnt.as<unsigned int>();
-      sa.nb_heavy = plan.nb_heavy;
-      sa.nb_medium = plan.nb_medium;
       // x of the final pass goes to the residue buffer (free after the conversion)
       u64* zcur = za;
       u64* znext = zb;
@@ -737,9 +739,9 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
           sa.x_out = (j == S - 1) ? r : nullptr;
           // after two passes rows without in-edges hold their constant value in
           // both buffers; the pass that writes x still covers every row
-          sa.n = (sweeps + j >= 2 && !sa.x_out) ? n_nz : (int32_t)n;
-          sa.resid = resid + (size_t)(sweeps + j) * 16;
-          launch_sweep<KT>(sa, plan, st);
+          sa.n_items = (sweeps + j >= 2 && !sa.x_out) ? plan.n_items_nz : plan.n_items_all;
+          sa.resid = resid + (size_t)(sweeps + j) * 64;
+          launch_sweep<KT>(sa, sweep_grid, st);
           std::swap(zcur, znext);
         }
         PPR_CUDA_TRY(cudaEventRecord(es1, st));
@@ -747,7 +749,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
         sweeps += S;
         launches += S;
         sweep_launches += S;
-        PPR_CUDA_TRY(cudaMemcpyAsync(hpin, resid + (size_t)(sweeps - 1) * 16, 16 * 8, cudaMemcpyDeviceToHost, st));
+        PPR_CUDA_TRY(cudaMemcpyAsync(hpin, resid + (size_t)(sweeps - 1) * 64, 64 * 8, cudaMemcpyDeviceToHost, st));
         PPR_CUDA_TRY(cudaStreamSynchronize(st));
         {
           float a = 0.f;
@@ -781,13 +783,14 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
       }
     }
     PPR_CUDA_TRY(cudaEventRecord(ev2, st));
-    PPR_CUDA_TRY(cudaMemsetAsync(counters + 64, 0, 8 * KT, st));
-    output_kernel<KT><<<grid_ew, 256, 0, st>>>(n, g->d_new_of_old, xfinal, ncols, t0, out_pi_dev, counters + 64);
-    ++launches;
+    PPR_CUDA_TRY(cudaMemsetAsync(mass, 0, 8 * KT, st));
+    output_kernel<KT><<<grid_ew, 256, 0, st>>>(n, g->d_new_of_old, xfinal, ncols, t0, out_pi_dev);
+    column_sum_kernel<KT><<<grid_ew, 256, 0, st>>>(n, xfinal, mass);
+    launches += 2;
     if (!need_dense && out_r)  // the queue phase finished: its residue is the answer's residual
-      output_kernel<KT><<<grid_ew, 256, 0, st>>>(n, g->d_new_of_old, r, ncols, t0, out_r_dev, counters + 96), ++launches;
+      output_kernel<KT><<<grid_ew, 256, 0, st>>>(n, g->d_new_of_old, r, ncols, t0, out_r_dev), ++launches;
     PPR_CUDA_TRY(cudaGetLastError());
-    PPR_CUDA_TRY(cudaMemcpyAsync(hpin, counters + 64, 8 * KT, cudaMemcpyDeviceToHost, st));
+    PPR_CUDA_TRY(cudaMemcpyAsync(hpin, mass, 8 * KT, cudaMemcpyDeviceToHost, st));
     PPR_CUDA_TRY(cudaStreamSynchronize(st));
     float a1 = 0, a2 = 0;
     cudaEventElapsedTime(&a1, ev0, ev1);
@@ -830,7 +833,11 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
 ppr_status query_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query_opts& o, double* out_pi,
                     double* out_r, ppr_stats* stats, cudaStream_t st) {
   int kt = o.k_tile;
-  if (kt == 0) kt = k >= 8 ? 8 : (k >= 4 ? 4 : (k >= 2 ? 2 : 1));
+  if (kt == 0) {
+    // one pass per tile: a wider tile costs less per source than two narrow ones
+    kt = 1;
+    while (kt < k && kt < 64) kt <<= 1;
+  }
   if ((size_t)g->n * kt >= ((size_t)1 << 32)) {
     set_error("n * k_tile must stay below 2^32");
     return PPR_ERR_ARG;
@@ -841,7 +848,9 @@ ppr_status query_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query
     case 4: return run_hp<4>(g, src, k, o, out_pi, out_r, stats, st);
     case 8: return run_hp<8>(g, src, k, o, out_pi, out_r, stats, st);
     case 16: return run_hp<16>(g, src, k, o, out_pi, out_r, stats, st);
-    default: set_error("k_tile must be 0, 1, 2, 4, 8 or 16"); return PPR_ERR_ARG;
+    case 32: return run_hp<32>(g, src, k, o, out_pi, out_r, stats, st);
+    case 64: return run_hp<64>(g, src, k, o, out_pi, out_r, stats, st);
+    default: set_error("k_tile must be 0, 1, 2, 4, 8, 16, 32 or 64"); return PPR_ERR_ARG;
   }
 }
 

@@ -86,6 +86,14 @@ struct ppr_graph {
   int32_t* d_piece_e0 = nullptr;
   int32_t* d_heavy_npieces = nullptr;
   uint32_t stamp_epoch = 0;
+  // per tile width: the sweep work list (index = log2 of the tile width, widths 1..64)
+  struct SweepPlan {
+    int kt = 0;
+    int32_t n_items_all = 0, n_items_nz = 0;
+    int32_t n_split = 0;          // rows cut into pieces (the first n_split rows)
+    int4* d_items = nullptr;
+    int32_t* d_npieces = nullptr; // pieces per split row
+  } plans[7];
   ppr::Workspace ws;
 };
 

@@ -56,7 +56,7 @@ def check_bound_and_mass(st, lam=LAM):
         assert -1e-15 <= s["mass_deficit"] <= s["final_l1_residual"] + 1e-15
 
 
-@pytest.mark.parametrize("k_tile", [1, 2, 4, 8])
+@pytest.mark.parametrize("k_tile", [1, 2, 4, 8, 16, 32, 64])
 def test_c0_chung_lu_against_powerpush(P, c0, c0_ref, k_tile):
     rp, ci, src = c0
     pi, st = run(P, rp, ci, src, k_tile=k_tile)
