@@ -82,6 +82,7 @@ typedef struct {
   double ms_total;              /* device time of the whole call */
   int64_t kernel_launches;      /* kernels this call launched */
   int64_t sweep_launches;       /* of which sweep-kernel launches */
+  double W;                     /* APPROX: walk budget of Eq. 8 (natural log) */
 } ppr_stats;
 
 /* Fill opts with defaults: alpha 0.2, lambda 1e-8, eps 0.5, mu 0 (=1/n),

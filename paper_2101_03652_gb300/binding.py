@@ -61,6 +61,7 @@ class ppr_stats(ctypes.Structure):
         ("ms_total", ctypes.c_double),
         ("kernel_launches", ctypes.c_int64),
         ("sweep_launches", ctypes.c_int64),
+        ("W", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -437,7 +437,7 @@ __global__ void residual_kernel(int32_t n, const int32_t* __restrict__ in_rp, co
 }
 
 // ------------------------------------------------------------ host engine
-static int sm_count() {
+int sm_count() {
   static int cached = 0;
   if (!cached) {
     int dev = 0;
@@ -454,6 +454,20 @@ static int sm_count() {
 // grouped so that every item costs about kItemPeriods periods.  Items are
 // ordered split pieces, medium rows, light rows, rows without in-edges.
 using Plan = ppr_graph::SweepPlan;
+
+static ppr_status build_plan(ppr_graph* g, int kt, Plan& p, cudaStream_t st);
+
+// work list for `lanes` lanes per row slice (shared with the FP32 sweeps)
+ppr_status get_plan(ppr_graph* g, int lanes, ppr_graph::SweepPlan** out, cudaStream_t st) {
+  int slot = 0;
+  while ((1 << slot) < lanes) ++slot;
+  if (slot > 5) { set_error("too many lanes per row"); return PPR_ERR_ARG; }
+  Plan& p = g->plans[slot + 1];
+  const int kt = lanes * 2;
+  if (p.kt != kt) PPR_TRY(build_plan(g, kt, p, st));
+  *out = &p;
+  return PPR_OK;
+}
 
 static ppr_status build_plan(ppr_graph* g, int kt, Plan& p, cudaStream_t st) {
   const std::vector<int32_t>& d = g->h_in_deg_sorted;
@@ -558,10 +572,9 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
   PPR_TRY(ws.ent_rem.ensure(cells * 4));
   PPR_TRY(ws.chunks.ensure((cells + (size_t)m * KT / kPushChunk + 64) * 8));
   static_assert(KT >= 1 && KT <= 64 && (KT & (KT - 1)) == 0, "tile width must be a power of two <= 64");
-  int plan_slot = 0;
-  while ((1 << plan_slot) < KT) ++plan_slot;
-  Plan& plan = g->plans[plan_slot];
-  if (plan.kt != KT) PPR_TRY(build_plan(g, KT, plan, st));
+  Plan* plan_p = nullptr;
+  PPR_TRY(get_plan(g, Lay<KT>::L, &plan_p, st));
+  Plan& plan = *plan_p;
   const size_t acc_bytes = std::max<size_t>((size_t)plan.n_split * KT * 8, 8);
   const size_t cnt_bytes = std::max<size_t>((size_t)plan.n_split * 4, 4);
   bool fresh_heavy = ws.heavy_acc.bytes < acc_bytes || ws.heavy_cnt.bytes < cnt_bytes;
