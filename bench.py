@@ -106,7 +106,7 @@ def sweep_bytes(n: int, m: int, kt: int) -> int:
 
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    for name in ("hp.cu", "ppr_internal.cuh"):
+    for name in ("sweep_kernel.cuh",):
         with open(os.path.join(ROOT, "paper_2101_03652_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

@@ -63,7 +63,8 @@ typedef struct {
                               queue phase (sweeps from the start) */
   int32_t max_sweeps;      /* bound on dense sweeps; 0 = 4*ceil(ln lambda/ln(1-alpha))+64 */
   int32_t reserved;
-  const void* warm_start;  /* reserved for a learned initial estimate; must be NULL */
+  const void* warm_start;  /* HP only: a ppr_model* of the same graph, or NULL for the
+                              zero start; the queue phase is skipped when set */
 } ppr_query_opts;
 
 typedef struct {
@@ -128,6 +129,67 @@ const char* ppr_last_error(void);
 /* Graph sizes: n, m as loaded. */
 int64_t ppr_graph_n(const ppr_graph* g);
 int64_t ppr_graph_m(const ppr_graph* g);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start.  The paper always starts from r = e_s; here a model
+ * maps a two-step sketch of the source (reserve after two Power Iterations,
+ * Eq. 5, plus the alive mass of Eq. 3 at step 2) projected by a fixed Gaussian
+ * n x 128 matrix through an MLP 128 -> hidden -> hidden -> 64 (GELU) to
+ * coefficients h, and returns x = max(0, S + U h) / sum (U: n x 64 basis).
+ * ppr_sssp_query with opts->warm_start = model pushes the residual of x,
+ * r = (alpha e_s + (1-alpha) x P - x) / alpha, to lambda exactly as it pushes
+ * e_s from the zero start, so the l1 guarantee does not depend on the model.
+ * Weights and U are FP32 masters with BF16 copies used by tensor-core GEMMs
+ * (FP32 accumulation); training minimises the mean l1 error ||x - pi||_1
+ * against exact vectors computed by the plain method, with Adam.
+ * ------------------------------------------------------------------------ */
+typedef struct ppr_model ppr_model;
+
+typedef struct {
+  int32_t feat_dim;  /* 128 */
+  int32_t hidden;    /* hidden width, multiple of 16 (512) */
+  int32_t rank;      /* basis rank, 64 */
+  int32_t reserved;
+  uint64_t seed;     /* weight init and Gaussian feature matrix */
+  float lr;          /* Adam step size (1e-3) */
+  int32_t epochs;    /* epochs for ppr_model_train (20) */
+  double alpha;      /* 0.2 */
+  double lambda;     /* labels' l1 accuracy (1e-8) */
+} ppr_model_opts;
+
+void ppr_model_default_opts(ppr_model_opts* opts);
+
+/* New model for graph g (init: W ~ N(0, 1/fan_in), b = 0, U = 0, so the
+ * untrained model returns the sketch).  Errors: PPR_ERR_ARG, PPR_ERR_OOM. */
+ppr_status ppr_model_create(ppr_graph* g, const ppr_model_opts* opts, ppr_model** out);
+
+/* Train on n_src sources (host ids): exact labels from the plain HP method
+ * (kept on the device, n x n_src FP32), then `epochs` passes of Adam over
+ * batches of 64 sources in a shuffled order.  loss_per_epoch: optional host
+ * array of `epochs` mean l1 losses.  Errors: PPR_ERR_ARG, PPR_ERR_ADMIT. */
+ppr_status ppr_model_train(ppr_model* model, const int32_t* train_src, int32_t n_src, int32_t epochs, float lr,
+                           uint64_t shuffle_seed, float* loss_per_epoch, void* cuda_stream);
+
+/* One forward/backward over k <= 64 sources with labels (k x n float64, host
+ * or device, caller's node order); lr > 0 also applies one Adam step.  loss
+ * receives the mean l1 error of the batch. */
+ppr_status ppr_model_train_step(ppr_model* model, const int32_t* src, int32_t k, const double* labels, float lr,
+                                double* loss, void* cuda_stream);
+
+/* The model's estimate x for k sources (k x n float64, host or device). */
+ppr_status ppr_model_estimate(ppr_model* model, const int32_t* src, int32_t k, double* out_x, void* cuda_stream);
+
+/* Parameters and last gradients, flat float32 in the order W1 (feat x hidden),
+ * b1, W2 (hidden x hidden), b2, W3 (hidden x rank), b3, U (n x rank, caller's
+ * node order); either pointer may be NULL. */
+int64_t ppr_model_param_count(const ppr_model* model);
+ppr_status ppr_model_get_params(const ppr_model* model, float* params, float* grads);
+ppr_status ppr_model_set_params(ppr_model* model, const float* params);
+
+/* Checkpoint (parameters and Adam moments) to a binary file, and back. */
+ppr_status ppr_model_save(const ppr_model* model, const char* path);
+ppr_status ppr_model_load(ppr_graph* g, const char* path, ppr_model** out);
+void ppr_model_free(ppr_model* model);
 
 #ifdef __cplusplus
 }

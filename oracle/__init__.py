@@ -83,6 +83,8 @@ def _load():
                 f.restype = ctypes.c_int
             lib.orc_philox4x32_10.argtypes = [P, P, P]
             lib.orc_philox4x32_10.restype = None
+            lib.orc_gaussian_rows.argtypes = [I64, I64, ctypes.c_int, U64, P]
+            lib.orc_gaussian_rows.restype = None
             lib.orc_speedppr_W.argtypes = [I64, D, D]
             lib.orc_speedppr_W.restype = D
             _lib = lib
@@ -227,3 +229,10 @@ def speedppr(g: Graph, s: int, eps: float = 0.5, mu: float | None = None, seed: 
     _rc(_load().orc_speedppr(*g.args(), alpha, s, eps, mu, seed, source_index, pi.ctypes.data, r.ctypes.data,
                              counts.ctypes.data, ctypes.byref(st)), "speedppr")
     return pi, r, counts, st.as_dict()
+
+
+def gaussian_rows(u0: int, count: int, F: int, seed: int) -> np.ndarray:
+    """Rows u0..u0+count-1 of the warm start's fixed Gaussian feature matrix."""
+    out = np.zeros((count, F))
+    _load().orc_gaussian_rows(u0, count, F, seed, out.ctypes.data)
+    return out

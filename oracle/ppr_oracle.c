@@ -25,6 +25,8 @@
  *   orc_walks           SpeedPPR's walk phase, Algorithm 4 (loop over v with r>0)
  *   orc_speedppr        Algorithm 4 end to end
  *   orc_philox4x32_10   Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+ *   orc_gaussian_rows   rows of the fixed random feature matrix of the learned
+ *                       warm start (Box-Muller on Philox words)
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -503,4 +505,34 @@ int orc_speedppr(int64_t n, const int64_t* rp, const int32_t* ci, double alpha, 
   }
   free(r); free(est); free(cnt);
   return rc;
+}
+
+/* ------------------------------------------------ warm-start feature matrix */
+/*
+ * Row u of the n x F feature matrix G used to project the two-step sketch:
+ * entry (u, j) is a standard normal.  Philox-4x32-10 with key (seed_lo,
+ * seed_hi) and counter (u, j/4, 0x47, 0) gives words w0..w3; (w0, w1) make
+ * entries 4q, 4q+1 and (w2, w3) make 4q+2, 4q+3 by Box-Muller (Box & Muller,
+ * 1958): u1 = (wa + 1) 2^-32 in (0, 1], u2 = wb 2^-32, radius
+ * sqrt(-2 ln u1), angles 2 pi u2 (cosine first, then sine).  F % 4 == 0.
+ * Writes rows u0 .. u0+count-1 into out (count x F, row-major).
+ */
+void orc_gaussian_rows(int64_t u0, int64_t count, int F, uint64_t seed, double* out) {
+  const double two_pi = 6.283185307179586476925286766559;
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int64_t i = 0; i < count; ++i) {
+    uint64_t u = (uint64_t)(u0 + i);
+    for (int q = 0; q < F / 4; ++q) {
+      uint32_t ctr[4] = {(uint32_t)u, (uint32_t)q, 0x47u, 0u};
+      uint32_t w[4];
+      orc_philox4x32_10(ctr, key, w);
+      for (int p = 0; p < 2; ++p) {
+        double u1 = ((double)w[2 * p] + 1.0) * (1.0 / 4294967296.0);
+        double u2 = (double)w[2 * p + 1] * (1.0 / 4294967296.0);
+        double rad = sqrt(-2.0 * log(u1));
+        out[i * F + 4 * q + 2 * p] = rad * cos(two_pi * u2);
+        out[i * F + 4 * q + 2 * p + 1] = rad * sin(two_pi * u2);
+      }
+    }
+  }
 }

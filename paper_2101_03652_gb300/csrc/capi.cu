@@ -24,7 +24,6 @@ ppr_status ppr_sssp_query(ppr_graph* g, const int32_t* src, int32_t k, ppr_mode 
   ppr_query_opts o;
   if (opts) o = *opts; else ppr_default_opts(&o);
   if (!(o.alpha > 0.0 && o.alpha < 1.0)) { set_error("alpha must lie in (0, 1)"); return PPR_ERR_ARG; }
-  if (o.warm_start) { set_error("warm_start is not supported by this entry point"); return PPR_ERR_ARG; }
   if (o.max_sweeps < 0 || o.switch_edges < -1) { set_error("max_sweeps/switch_edges out of range"); return PPR_ERR_ARG; }
   for (int32_t i = 0; i < k; ++i)
     if (src[i] < 0 || src[i] >= g->n) {
@@ -41,6 +40,7 @@ ppr_status ppr_sssp_query(ppr_graph* g, const int32_t* src, int32_t k, ppr_mode 
   } else if (mode == PPR_APPROX) {
     if (!(o.eps > 0.0) || !std::isfinite(o.eps)) { set_error("eps must be > 0"); return PPR_ERR_ARG; }
     if (o.mu < 0.0 || o.mu > 1.0) { set_error("mu must lie in [0, 1] (0 means 1/n)"); return PPR_ERR_ARG; }
+    if (o.warm_start) { set_error("warm_start applies to HP mode only"); return PPR_ERR_ARG; }
   } else {
     set_error("unknown mode %d", (int)mode);
     return PPR_ERR_ARG;

@@ -106,4 +106,6 @@ ppr_status query_approx(ppr_graph* g, const int32_t* src, int32_t k, const ppr_q
 bool is_device_pointer(const void* p);
 ppr_status get_plan(ppr_graph* g, int lanes, ppr_graph::SweepPlan** out, cudaStream_t st);
 int sm_count();
+ppr_status warm_start_tile(const void* model, ppr_graph* g, const int32_t* src_new, int ncols, int kt, double alpha,
+                           unsigned long long* z0, cudaStream_t st);
 }  // namespace ppr
