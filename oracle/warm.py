@@ -71,17 +71,28 @@ def features(S: np.ndarray, F: int, seed: int) -> np.ndarray:
     return f
 
 
-def mlp_forward(f, W1, b1, W2, b2, W3, b3):
+def bf16(x):
+    """Round to bfloat16 (nearest, ties to even) through float32, back to float64."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def mlp_forward(f, W1, b1, W2, b2, W3, b3, rnd=None):
+    """rnd(x) rounds a tensor where the GPU feeds it to a BF16 GEMM (identity by default)."""
+    r = rnd or (lambda x: x)
+    f = r(f)
     a1 = f @ W1 + b1
-    h1 = gelu(a1)
+    h1 = r(gelu(a1))
     a2 = h1 @ W2 + b2
-    h2 = gelu(a2)
+    h2 = r(gelu(a2))
     h = h2 @ W3 + b3
     return h, (f, a1, h1, a2, h2)
 
 
-def basis_forward(S, U, h):
-    Z = S + U @ h.T
+def basis_forward(S, U, h, rnd=None):
+    r = rnd or (lambda x: x)
+    Z = S + r(U) @ r(h).T
     Y = np.maximum(Z, 0.0)
     sig = Y.sum(axis=0)
     X = np.where(sig > 0, Y / np.where(sig > 0, sig, 1.0), S)
@@ -92,17 +103,21 @@ def loss(X, pi):
     return np.abs(X - pi).sum() / X.shape[1]
 
 
-def forward(params, S, f):
+def forward(params, S, f, rnd=None):
     W1, b1, W2, b2, W3, b3, U = params
-    h, mcache = mlp_forward(f, W1, b1, W2, b2, W3, b3)
-    X, bcache = basis_forward(S, U, h)
+    r = rnd or (lambda x: x)
+    h, mcache = mlp_forward(f, r(W1), b1, r(W2), b2, r(W3), b3, rnd)
+    X, bcache = basis_forward(S, U, h, rnd)
     return X, h, mcache, bcache
 
 
-def backward(params, S, f, pi):
-    """Loss and gradients (subgradient sign(X - pi) of the l1 loss)."""
-    W1, b1, W2, b2, W3, b3, U = params
-    X, h, (f_, a1, h1, a2, h2), (Z, sig) = forward(params, S, f)
+def backward(params, S, f, pi, rnd=None):
+    """Loss and gradients (subgradient sign(X - pi) of the l1 loss).  With rnd,
+    the forward pass rounds where the GPU does and the backward pass uses the
+    rounded tensors; gradients themselves stay float64."""
+    r = rnd or (lambda x: x)
+    W1, b1, W2, b2, W3, b3, U = [r(p) if i in (0, 2, 4, 6) else p for i, p in enumerate(params)]
+    X, h, (f_, a1, h1, a2, h2), (Z, sig) = forward([W1, b1, W2, b2, W3, b3, U], S, f, rnd)
     B = X.shape[1]
     L = loss(X, pi)
     dX = np.sign(X - pi) / B
@@ -123,9 +138,22 @@ def backward(params, S, f, pi):
     return L, [dW1, db1, dW2, db2, dW3, db3, dU]
 
 
-def warm_estimate(g: Graph, src, params, F: int, seed: int, alpha: float = 0.2) -> np.ndarray:
+def warm_estimate(g: Graph, src, params, F: int, seed: int, alpha: float = 0.2, rnd=None) -> np.ndarray:
     """X for a batch of sources (n x B)."""
     S = sketches(g, src, alpha)
     f = features(S, F, seed)
-    X, *_ = forward(params, S, f)
+    X, *_ = forward(params, S, f, rnd)
     return X
+
+
+def unflatten(flat, n: int, F: int = 128, H: int = 512, R: int = 64):
+    """Split the library's flat parameter order W1, b1, W2, b2, W3, b3, U."""
+    flat = np.asarray(flat, dtype=np.float64)
+    shapes = [(F, H), (H,), (H, H), (H,), (H, R), (R,), (n, R)]
+    out, o = [], 0
+    for sh in shapes:
+        cnt = int(np.prod(sh))
+        out.append(flat[o:o + cnt].reshape(sh))
+        o += cnt
+    assert o == len(flat)
+    return out

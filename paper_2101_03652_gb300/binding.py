@@ -68,6 +68,20 @@ class ppr_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ppr_model_opts(ctypes.Structure):
+    _fields_ = [
+        ("feat_dim", ctypes.c_int32),
+        ("hidden", ctypes.c_int32),
+        ("rank", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("lr", ctypes.c_float),
+        ("epochs", ctypes.c_int32),
+        ("alpha", ctypes.c_double),
+        ("lambda_", ctypes.c_double),
+    ]
+
+
 # every symbol include/ppr.h declares, with its ctypes signature
 _P = ctypes.c_void_p
 SIGNATURES = {
@@ -79,6 +93,18 @@ SIGNATURES = {
     "ppr_last_error": (ctypes.c_char_p, []),
     "ppr_graph_n": (ctypes.c_int64, [_P]),
     "ppr_graph_m": (ctypes.c_int64, [_P]),
+    "ppr_model_default_opts": (None, [ctypes.POINTER(ppr_model_opts)]),
+    "ppr_model_create": (ctypes.c_int, [_P, ctypes.POINTER(ppr_model_opts), ctypes.POINTER(_P)]),
+    "ppr_model_train": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_uint64,
+                                       _P, _P]),
+    "ppr_model_train_step": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, ctypes.c_float, _P, _P]),
+    "ppr_model_estimate": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
+    "ppr_model_param_count": (ctypes.c_int64, [_P]),
+    "ppr_model_get_params": (ctypes.c_int, [_P, _P, _P]),
+    "ppr_model_set_params": (ctypes.c_int, [_P, _P]),
+    "ppr_model_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "ppr_model_load": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.POINTER(_P)]),
+    "ppr_model_free": (None, [_P]),
 }
 
 _lock = threading.Lock()
@@ -186,12 +212,93 @@ class Graph:
         except Exception:
             pass
 
-    def query(self, src, mode: int = PPR_HP, out_pi=None, out_r=None, out_walk_counts=None, stream=None, **opts):
-        """Returns (pi, stats); pi is a (k, n) float64 CUDA tensor unless out_pi is given."""
+    def query(self, src, mode: int = PPR_HP, out_pi=None, out_r=None, out_walk_counts=None, stream=None,
+              warm_start=None, **opts):
+        """Returns (pi, stats); pi is a (k, n) float64 CUDA tensor unless out_pi is given.
+        warm_start: a Model of this graph (HP only)."""
         import torch
         k = len(src)
         if out_pi is None:
             out_pi = torch.empty((k, self.n), dtype=torch.float64, device="cuda")
         o = ppr_default_opts(**opts)
+        if warm_start is not None:
+            o.warm_start = warm_start.handle
         stats = ppr_sssp_query(self.handle, src, mode, o, out_pi, out_r, out_walk_counts, True, stream)
         return out_pi, stats
+
+
+def ppr_model_default_opts(**kw) -> ppr_model_opts:
+    o = ppr_model_opts()
+    load_library().ppr_model_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, "lambda_" if k == "lam" else k, v)
+    return o
+
+
+class Model:
+    """Learned warm start of a Graph (see include/ppr.h)."""
+
+    def __init__(self, graph: Graph, handle=None, **opts):
+        self.graph = graph
+        if handle is None:
+            h = ctypes.c_void_p()
+            o = ppr_model_default_opts(**opts)
+            _check(load_library().ppr_model_create(graph.handle, ctypes.byref(o), ctypes.byref(h)))
+            handle = h.value
+        self.handle = handle
+
+    @classmethod
+    def load(cls, graph: Graph, path: str) -> "Model":
+        h = ctypes.c_void_p()
+        _check(load_library().ppr_model_load(graph.handle, path.encode(), ctypes.byref(h)))
+        return cls(graph, handle=h.value)
+
+    def save(self, path: str):
+        _check(load_library().ppr_model_save(self.handle, path.encode()))
+
+    def close(self):
+        if self.handle:
+            load_library().ppr_model_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def train(self, src, epochs: int, lr: float = 1e-3, shuffle_seed: int = 0, stream=None):
+        s = np.ascontiguousarray(src, dtype=np.int32)
+        losses = np.zeros(max(epochs, 1), dtype=np.float32)
+        _check(load_library().ppr_model_train(self.handle, s.ctypes.data, len(s), epochs, lr, shuffle_seed,
+                                              losses.ctypes.data, _stream(stream)))
+        return losses[:epochs]
+
+    def train_step(self, src, labels, lr: float = 0.0, stream=None) -> float:
+        s = np.ascontiguousarray(src, dtype=np.int32)
+        loss = ctypes.c_double()
+        _check(load_library().ppr_model_train_step(self.handle, s.ctypes.data, len(s), _ptr(labels), lr,
+                                                   ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+    def estimate(self, src, out=None, stream=None):
+        s = np.ascontiguousarray(src, dtype=np.int32)
+        if out is None:
+            out = np.zeros((len(s), self.graph.n))
+        _check(load_library().ppr_model_estimate(self.handle, s.ctypes.data, len(s), _ptr(out), _stream(stream)))
+        return out
+
+    def param_count(self) -> int:
+        return load_library().ppr_model_param_count(self.handle)
+
+    def get_params(self, grads: bool = False):
+        cnt = self.param_count()
+        p = np.zeros(cnt, dtype=np.float32)
+        g = np.zeros(cnt, dtype=np.float32) if grads else None
+        _check(load_library().ppr_model_get_params(self.handle, p.ctypes.data, g.ctypes.data if grads else None))
+        return (p, g) if grads else p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert len(p) == self.param_count()
+        _check(load_library().ppr_model_set_params(self.handle, p.ctypes.data))

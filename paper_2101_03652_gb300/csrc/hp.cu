@@ -586,6 +586,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
         R = 0.0;
         for (int c = 0; c < ncols; ++c) {
           double Dc = D[c] / kFixOne / alpha;
+          if (!std::isfinite(r0[c])) r0[c] = Dc;  // warm start: measured ||r(x0)||_1
           bound[c] = (1.0 - alpha) * Dc * (1.0 + 1e-4) + 2.0 * slack;
           if (bound[c] > lambda) ok = false;
           R = std::max(R, bound[c]);
