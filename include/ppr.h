@@ -120,6 +120,34 @@ ppr_status ppr_sssp_query(ppr_graph* g, const int32_t* src, int32_t k, ppr_mode 
                           const ppr_query_opts* opts, double* out_pi, double* out_r,
                           uint32_t* out_walk_counts, ppr_stats* stats, void* cuda_stream);
 
+/*
+ * High-precision queries without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that may not allocate
+ * device memory themselves or through this library -- for example a plug-in
+ * inside a server or database that gets a fixed memory budget from its host's
+ * own allocator, or a process that has already reserved all free memory in a
+ * caching pool.  ppr_sssp_query grows a per-graph workspace with cudaMalloc;
+ * this call instead runs a simpler variant of the pull sweep (zero start,
+ * every node pushed each pass, Sec. 4.1 / Lemma 1) whose scratch is one
+ * 16 MiB array compiled into the library, and it calls no allocation routine.
+ *   src: host int32[k]; out_pi: DEVICE k x n float64 (caller-owned);
+ *   out_sweeps: optional host int32[k] (passes run for each source).
+ *   Result: ||pi_hat - pi||_1 <= lambda for every source, as ppr_sssp_query.
+ * Limit: n * min(k, 8) rounded to a power of two, times 24 bytes, plus a few
+ * kilobytes, must fit in the 16 MiB (about 87,000 nodes for 8 sources at a
+ * time, 690,000 for one); larger graphs return PPR_ERR_ARG with a message.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before capturing any stream on the device.  All calls share the one array
+ * (it keeps the last call's contents; the call clears what must start at
+ * zero), so calls that overlap on the GPU -- other threads, other streams --
+ * race and must be serialised by the caller.  The graph itself is allocated
+ * by ppr_graph_load as usual.  Errors: PPR_ERR_ARG, PPR_ERR_NOT_CONVERGED,
+ * PPR_ERR_CUDA.
+ */
+ppr_status ppr_sssp_query_noalloc(ppr_graph* g, const int32_t* src, int32_t k, double alpha, double lambda,
+                                  double* out_pi, int32_t* out_sweeps, void* cuda_stream);
+
 /* Release the graph and every device buffer it owns; NULL is allowed. */
 void ppr_free(ppr_graph* g);
 

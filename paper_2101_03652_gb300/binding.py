@@ -90,6 +90,8 @@ SIGNATURES = {
     "ppr_sssp_query": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int, ctypes.POINTER(ppr_query_opts),
                                       _P, _P, _P, _P, _P]),
     "ppr_free": (None, [_P]),
+    "ppr_sssp_query_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _P, _P,
+                                              _P]),
     "ppr_last_error": (ctypes.c_char_p, []),
     "ppr_graph_n": (ctypes.c_int64, [_P]),
     "ppr_graph_m": (ctypes.c_int64, [_P]),
@@ -186,6 +188,17 @@ def ppr_sssp_query(graph: int, src, mode: int, opts: ppr_query_opts, out_pi, out
     _check(load_library().ppr_sssp_query(graph, s.ctypes.data, len(s), mode, ctypes.byref(opts), _ptr(out_pi),
                                          _ptr(out_r), _ptr(out_walk_counts), st, _stream(stream)))
     return [x.as_dict() for x in st] if stats else None
+
+
+def ppr_sssp_query_noalloc(graph: int, src, out_pi, alpha: float = 0.2, lam: float = 1e-8, stream=None):
+    """High-precision queries through the entry point that allocates nothing
+    (scratch compiled into the library); out_pi must be a (k, n) float64 CUDA
+    tensor.  Returns the passes run per source."""
+    s = np.ascontiguousarray(src, dtype=np.int32)
+    sweeps = np.zeros(len(s), dtype=np.int32)
+    _check(load_library().ppr_sssp_query_noalloc(graph, s.ctypes.data, len(s), alpha, lam, _ptr(out_pi),
+                                                 sweeps.ctypes.data, _stream(stream)))
+    return sweeps
 
 
 def ppr_free(graph: int):
