@@ -244,6 +244,11 @@ def run_gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_total = float(t.item())
 
+    # learned warm start (model trained on the workload's graph, held-out sources)
+    warm = None
+    if not args.skip_warm and args.workload == "rmat20-k64":
+        warm = warm_start_comparison(P, g, n, k, kt, out, flush, rank)
+
     # sanity of the last answers (the parity tests check them against the oracle)
     pi0 = out[0].double()
     mass = float(pi0.sum().item())
@@ -289,6 +294,7 @@ def run_gpu(args):
                      "traffic": ncu_traffic(args.workload), "algorithmic_bytes_per_launch": per_launch,
                      "avg_launch_ms": avg_sweep_ms},
         "cpu_baseline": cpu,
+        "warm_start": warm,
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
@@ -296,6 +302,44 @@ def run_gpu(args):
     g.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+def warm_start_comparison(P, g, n, k, kt, out, flush, rank, train_n=4096, held_n=1024, epochs=8, passes=8):
+    """Train the learned warm start on train_n sources (seed 4) and compare
+    queries/s and passes on held_n held-out sources (seed 5) with the plain
+    zero start, same batches of k sources, L2 flushed before each batch."""
+    import numpy as np
+    import torch
+    import ppr_inputs as gen
+    train = gen.sources(n, train_n, seed=4)
+    held = gen.sources(n, held_n, seed=5 + 1000 * rank)
+    model = P.Model(g, seed=0x5EED, correction_passes=passes)
+    t = time.perf_counter()
+    losses = model.train(train, epochs=epochs, lr=2e-3, shuffle_seed=1)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t
+    res = {}
+    for name, ws in (("plain", None), ("warm", model)):
+        ev = []
+        sweeps = []
+        g.query(held[:k], P.PPR_HP, out_pi=out, lam=LAMBDA, k_tile=kt, warm_start=ws)  # warm-up
+        for b in range(0, held_n, k):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, st = g.query(held[b:b + k], P.PPR_HP, out_pi=out, lam=LAMBDA, k_tile=kt, warm_start=ws)
+            e1.record()
+            ev.append((e0, e1))
+            sweeps.append(st[0]["sweeps"])
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        res[name] = {"queries_per_s": held_n / (ms / 1e3), "passes_mean": float(np.mean(sweeps))}
+    model.close()
+    return {"metric": "queries/s at l1<=1e-8 on held-out sources", "train_sources": train_n,
+            "held_out_sources": held_n, "epochs": epochs, "correction_passes": passes,
+            "train_seconds_incl_labels": train_s, "final_train_l1": float(losses[-1]),
+            "plain": res["plain"], "warm": res["warm"],
+            "speedup": res["warm"]["queries_per_s"] / res["plain"]["queries_per_s"]}
 
 
 def main():
@@ -306,6 +350,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat20-k64", choices=sorted(WORKLOADS))
     ap.add_argument("--skip-cpu", action="store_true", help="omit the oracle CPU baseline")
+    ap.add_argument("--skip-warm", action="store_true", help="omit the learned warm-start comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

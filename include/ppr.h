@@ -42,6 +42,8 @@ typedef enum {
   PPR_ERR_ADMIT = -6          /* not enough free device memory for the batch state */
 } ppr_status;
 
+#define PPR_FLAG_PARTIAL 1
+
 typedef enum {
   PPR_HP = 0,     /* high precision: ||pi_hat - pi||_1 <= lambda (PowerPush, Algorithm 3) */
   PPR_APPROX = 1  /* approximate: SpeedPPR, Algorithm 4 (FP32 push + Philox walks) */
@@ -62,7 +64,9 @@ typedef struct {
                               than this many out-edges over the tile; -1 = auto, 0 = no
                               queue phase (sweeps from the start) */
   int32_t max_sweeps;      /* bound on dense sweeps; 0 = 4*ceil(ln lambda/ln(1-alpha))+64 */
-  int32_t reserved;
+  int32_t flags;           /* HP: PPR_FLAG_PARTIAL returns the estimate after exactly
+                              max_sweeps passes without certifying lambda (the stats'
+                              final_l1_residual is then the bound reached) */
   const void* warm_start;  /* HP only: a ppr_model* of the same graph, or NULL for the
                               zero start; the queue phase is skipped when set */
 } ppr_query_opts;
@@ -177,7 +181,10 @@ typedef struct {
   int32_t feat_dim;  /* 128 */
   int32_t hidden;    /* hidden width, multiple of 16 (512) */
   int32_t rank;      /* basis rank, 64 */
-  int32_t reserved;
+  int32_t correction_passes; /* 0: x0 = max(0, S + U h)/sum replaces the zero start.
+                                L > 0: the zero-start solve runs L passes, then the
+                                model adds mu * max(0, U h)/sum, mu = 1 - sum(x) the
+                                mass still missing (the residual's sum becomes 0) */
   uint64_t seed;     /* weight init and Gaussian feature matrix */
   float lr;          /* Adam step size (1e-3) */
   int32_t epochs;    /* epochs for ppr_model_train (20) */

@@ -17,6 +17,7 @@ from . import _build
 PPR_OK, PPR_ERR_ARG, PPR_ERR_GRAPH, PPR_ERR_OOM = 0, -1, -2, -3
 PPR_ERR_NOT_CONVERGED, PPR_ERR_CUDA, PPR_ERR_ADMIT = -4, -5, -6
 PPR_HP, PPR_APPROX = 0, 1
+PPR_FLAG_PARTIAL = 1
 
 STATUS_NAMES = {0: "PPR_OK", -1: "PPR_ERR_ARG", -2: "PPR_ERR_GRAPH", -3: "PPR_ERR_OOM",
                 -4: "PPR_ERR_NOT_CONVERGED", -5: "PPR_ERR_CUDA", -6: "PPR_ERR_ADMIT"}
@@ -39,7 +40,7 @@ class ppr_query_opts(ctypes.Structure):
         ("epoch_num", ctypes.c_int32),
         ("switch_edges", ctypes.c_int64),
         ("max_sweeps", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
         ("warm_start", ctypes.c_void_p),
     ]
 
@@ -73,7 +74,7 @@ class ppr_model_opts(ctypes.Structure):
         ("feat_dim", ctypes.c_int32),
         ("hidden", ctypes.c_int32),
         ("rank", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("correction_passes", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
         ("lr", ctypes.c_float),
         ("epochs", ctypes.c_int32),

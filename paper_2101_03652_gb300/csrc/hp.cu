@@ -444,7 +444,12 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
     int levels = 0;
     bool all_done = false;
     bool have_state = false;  // (r, pi) hold a push state
-    const bool warm = o.warm_start != nullptr;  // a learned estimate replaces the queue phase
+    // a learned estimate either replaces the zero start (correction_passes = 0)
+    // or corrects the remaining mass after `corr` passes of the zero-start solve
+    const int corr = o.warm_start ? warm_correction_passes(o.warm_start) : 0;
+    const bool warm = o.warm_start != nullptr && corr == 0;
+    const bool partial = (o.flags & PPR_FLAG_PARTIAL) != 0;
+    bool corrected = false;
     if (switch_edges != 0 && !warm) {
       PPR_CUDA_TRY(cudaMemsetAsync(r, 0, cells * 8, st));
       PPR_CUDA_TRY(cudaMemsetAsync(pi, 0, cells * 8, st));
@@ -542,12 +547,22 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
       u64* znext = zb;
       double R = 0.0;
       for (int c = 0; c < ncols; ++c) R = std::max(R, r0[c]);
+      double rate = -1.0, prev_d = -1.0;  // observed contraction per pass
+      int prev_sweeps = 0;
+      bool probe_next = warm;             // warm start: learn the rate before a long batch
       while (true) {
-        // unknown residual (warm start): one pass measures it
-        int S = (!std::isfinite(R) || R <= lambda)
-                    ? 1
-                    : (int)std::ceil(std::log(lambda / R) / std::log(1.0 - alpha) - 1e-12);
+        // unknown residual (warm start): one pass measures it.  The residual
+        // contracts at least by (1-alpha) per pass; once two measurements exist
+        // the observed rate (faster after a learned correction) predicts the
+        // passes, and every stop is still certified by a measurement.
+        const double cr = rate > 0.0 ? rate : (1.0 - alpha);
+        int S = (!std::isfinite(R) || R <= lambda) ? 1
+                                                    : (int)std::ceil(std::log(lambda / R) / std::log(cr) - 1e-12);
         S = std::max(S, 1);
+        if (rate <= 0.0 && probe_next) S = std::min(S, 4);
+        if (corr > 0 && !corrected) S = std::max(corr - sweeps, 1);  // passes before the correction
+        if (partial) S = std::max(max_sweeps - sweeps, 0);
+        if (partial && S == 0) break;
         if (sweeps + S > max_sweeps) {
           set_error("sweep limit %d reached", max_sweeps);
           status = PPR_ERR_NOT_CONVERGED;
@@ -584,12 +599,34 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
         const double slack = (double)m * 0.5 / kFixOne / alpha;
         bool ok = true;
         R = 0.0;
+        double dmax = 0.0;
+        for (int c = 0; c < ncols; ++c) dmax = std::max(dmax, D[c] / kFixOne / alpha);
+        if (prev_d > 0.0 && dmax > 0.0 && dmax < prev_d && sweeps > prev_sweeps)
+          rate = std::min(1.0 - alpha, std::max(0.02, std::pow(dmax / prev_d, 1.0 / (sweeps - prev_sweeps))));
+        if (prev_d > 0.0 || !probe_next) probe_next = false;
+        prev_d = dmax;
+        prev_sweeps = sweeps;
         for (int c = 0; c < ncols; ++c) {
           double Dc = D[c] / kFixOne / alpha;
           if (!std::isfinite(r0[c])) r0[c] = Dc;  // warm start: measured ||r(x0)||_1
           bound[c] = (1.0 - alpha) * Dc * (1.0 + 1e-4) + 2.0 * slack;
           if (bound[c] > lambda) ok = false;
           R = std::max(R, bound[c]);
+        }
+        if (partial) break;
+        if (corr > 0 && !corrected) {
+          // add mu * q to x (mu = 1 - sum x, exact), rebuild z for the next pass;
+          // the residual's sum becomes zero and its norm is measured again
+          PPR_CUDA_TRY(cudaMemsetAsync(mass, 0, 8 * KT, st));
+          column_sum_kernel<KT><<<grid_ew, 256, 0, st>>>(n, r, mass);
+          PPR_TRY(warm_correct_tile(o.warm_start, g, src_new, ncols, KT, alpha, r, mass, zcur, st));
+          launches += 1;
+          corrected = true;
+          R = std::numeric_limits<double>::infinity();
+          rate = -1.0;        // the correction changes the residual: measure afresh
+          prev_d = -1.0;
+          probe_next = true;  // short first batch to learn the new contraction rate
+          continue;
         }
         if (ok) break;
       }

@@ -259,6 +259,9 @@ struct BasisArgs {
   int kt;
   const uint64_t* omega;
   float* Xout;          // pass 5 output: X as FP32 [n][B]
+  int with_sketch;      // Z = S + U h (1) or Z = U h (0: the model predicts a distribution)
+  const u64* xin;       // pass 6: current estimate [n][kt] (Q1.63)
+  const u64* mass;      // pass 6: [kt] exact sums of xin
 };
 
 template <int B, int PASS>
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(256) basis_kernel(BasisArgs a) {
         const int u = r0 + (i >= 2 ? 8 : 0), c = j * 8 + kq + (i & 1);
         if (u >= a.n || c >= a.ncols) continue;
         const float s = a.S[(size_t)u * B + c];
-        const float z = acc[j][i] + s;
+        const float z = acc[j][i] + (a.with_sketch ? s : 0.f);
         const float y = fmaxf(z, 0.f);
         if constexpr (PASS == 1) {
           part[j][i & 1] += y;
@@ -318,6 +321,15 @@ __global__ void __launch_bounds__(256) basis_kernel(BasisArgs a) {
             if (c < a.kt) a.z0[(size_t)u * a.kt + c] = hi + (lo >> 63);
           } else if constexpr (PASS == 5) {
             a.Xout[(size_t)u * B + c] = X;
+          } else if constexpr (PASS == 6) {
+            // x += mu X with mu = 1 - sum x (exact, raw units); z = x (1-alpha)/d
+            if (c < a.kt) {
+              const u64 mu = kFixOneRaw - a.mass[c];
+              const u64 xn = a.xin[(size_t)u * a.kt + c] + (u64)((double)mu * (double)X);
+              const u64 om = a.omega[u];
+              const u64 hi = __umul64hi(xn, om), lo = xn * om;
+              a.z0[(size_t)u * a.kt + c] = hi + (lo >> 63);
+            }
           } else {
             const float diff = X - a.pi[(size_t)u * a.ldpi + c];
             const float gsg = diff > 0.f ? a.invB : (diff < 0.f ? -a.invB : 0.f);
@@ -468,6 +480,7 @@ using namespace ppr;
 struct ppr_model {
   ppr_graph* g = nullptr;
   int F = 128, H = 512, R = kR;
+  int L = 0;  // correction passes (0: the estimate replaces the zero start)
   uint64_t seed = 0;
   int64_t n_params = 0, off_b1, off_W2, off_b2, off_W3, off_b3, off_U;
   float *p = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
@@ -596,6 +609,7 @@ static BasisArgs basis_args(ppr_model* md, int ncols) {
   ba.loss = md->loss_d;
   ba.dZb = md->dZb;
   ba.dU = md->grad + md->off_U;
+  ba.with_sketch = md->L == 0;
   return ba;
 }
 
@@ -641,7 +655,12 @@ static ppr_status model_step(ppr_model* md, const int32_t* src_new_host, int nco
     md->step += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - std::pow(b1, (float)md->step), c2 = 1.f - std::pow(b2, (float)md->step);
-    adam_kernel<<<sm_count() * 8, 256, 0, st>>>(md->n_params, md->p, md->m, md->v, md->grad, lr, b1, b2, 1e-8f, c1, c2);
+    // a correction model's basis holds a distribution spanning orders of
+    // magnitude: it takes smaller steps than the network
+    const float lr_u = md->L > 0 ? lr * 0.01f : lr;
+    adam_kernel<<<sm_count() * 8, 256, 0, st>>>(md->off_U, md->p, md->m, md->v, md->grad, lr, b1, b2, 1e-8f, c1, c2);
+    adam_kernel<<<sm_count() * 8, 256, 0, st>>>(md->n_params - md->off_U, md->p + md->off_U, md->m + md->off_U,
+                                                md->v + md->off_U, md->grad + md->off_U, lr_u, b1, b2, 1e-8f, c1, c2);
     PPR_TRY(refresh_bf16(md, st));
   }
   if (loss_out) {
@@ -689,6 +708,62 @@ ppr_status warm_start_tile(const void* model, ppr_graph* g, const int32_t* src_n
   return PPR_OK;
 }
 
+int warm_correction_passes(const void* model) { return ((const ppr_model*)model)->L; }
+
+// x + mu q for a solver tile, written as z = (x + mu q)(1-alpha)/d into z
+ppr_status warm_correct_tile(const void* model, ppr_graph* g, const int32_t* src_new, int ncols, int kt,
+                             double alpha, const unsigned long long* x, const unsigned long long* mass,
+                             unsigned long long* z, cudaStream_t st) {
+  ppr_model* md = (ppr_model*)model;
+  if (md->g != g) { set_error("warm_start model belongs to another graph"); return PPR_ERR_ARG; }
+  BasisArgs ba = basis_args(md, ncols);
+  ba.z0 = z;
+  ba.kt = kt;
+  ba.omega = g->d_omega;
+  ba.xin = x;
+  ba.mass = mass;
+  const int grid = sm_count() * 4;
+  if (kt <= 16) {
+    PPR_TRY(model_estimate_internal<16>(md, src_new, ncols, alpha, st));
+    basis_kernel<16, 6><<<grid, 256, 0, st>>>(ba);
+  } else if (kt <= 32) {
+    PPR_TRY(model_estimate_internal<32>(md, src_new, ncols, alpha, st));
+    basis_kernel<32, 6><<<grid, 256, 0, st>>>(ba);
+  } else {
+    PPR_TRY(model_estimate_internal<64>(md, src_new, ncols, alpha, st));
+    basis_kernel<64, 6><<<grid, 256, 0, st>>>(ba);
+  }
+  PPR_CUDA_TRY(cudaGetLastError());
+  return PPR_OK;
+}
+
+// start a correction model at the mean training target: U[u][0] = n * mean_c lab[u][c]
+// (the scale cancels in the normalisation), W3[:, 0] = 0 and b3[0] = 1 so that
+// h_0 = 1 for every source
+__global__ void mean_shape_kernel(int64_t n, int64_t ncols, const float* __restrict__ lab, int R,
+                                  float* __restrict__ U) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int64_t c = 0; c < ncols; ++c) s += lab[u * ncols + c];
+    U[u * R] = (float)(s / (double)ncols * (double)n);
+    for (int k = 1; k < R; ++k) U[u * R + k] = 0.f;
+  }
+}
+
+// correction labels: lab[new(o) * ld + col0 + c] = (pi - x_L)[c][o] / mu_c
+__global__ void correction_labels_kernel(int64_t n, int ncols, const double* __restrict__ pi,
+                                         const double* __restrict__ xl, const double* __restrict__ mu,
+                                         const int32_t* __restrict__ new_of_old, float* __restrict__ lab, int64_t ld,
+                                         int64_t col0) {
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = new_of_old[o];
+    for (int c = 0; c < ncols; ++c) {
+      const size_t i = (size_t)c * n + o;
+      lab[u * ld + col0 + c] = mu[c] > 0.0 ? (float)((pi[i] - xl[i]) / mu[c]) : 0.f;
+    }
+  }
+}
+
 }  // namespace ppr
 
 // ================================================================== C ABI
@@ -700,6 +775,7 @@ void ppr_model_default_opts(ppr_model_opts* o) {
   o->feat_dim = 128;
   o->hidden = 512;
   o->rank = 64;
+  o->correction_passes = 0;
   o->seed = 0x5eedull;
   o->lr = 1e-3f;
   o->epochs = 20;
@@ -722,7 +798,13 @@ ppr_status ppr_model_create(ppr_graph* g, const ppr_model_opts* opts, ppr_model*
   md->F = o.feat_dim;
   md->H = o.hidden;
   md->R = o.rank;
+  md->L = o.correction_passes;
   md->seed = o.seed;
+  if (md->L < 0 || md->L > 200) {
+    delete md;
+    set_error("correction_passes must lie in [0, 200]");
+    return PPR_ERR_ARG;
+  }
   ppr_status s = model_alloc(md);
   if (s != PPR_OK) { model_release(md); delete md; return s; }
   // init: W ~ N(0, 1/fan_in), b = 0, U = 0 (the untrained model returns the sketch)
@@ -737,8 +819,17 @@ ppr_status ppr_model_create(ppr_graph* g, const ppr_model_opts* opts, ppr_model*
   fill(md->off_W2, md->H, md->H);
   fill(md->off_W3, md->H, md->R);
   cudaStream_t st = nullptr;
+  // a correction model starts from the uniform distribution: U[:, 0] = 1, b3[0] = 1
+  if (md->L > 0) host[md->off_b3] = 1.f;
+  std::vector<float> u0;
+  if (md->L > 0) {
+    u0.assign((size_t)g->n * md->R, 0.f);
+    for (int64_t u = 0; u < g->n; ++u) u0[(size_t)u * md->R] = 1.f;
+  }
   if (cudaMemcpy(md->p, host.data(), sizeof(float) * host.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(md->p + md->off_U, 0, sizeof(float) * g->n * md->R) != cudaSuccess ||
+      (md->L > 0 && cudaMemcpy(md->p + md->off_U, u0.data(), sizeof(float) * u0.size(), cudaMemcpyHostToDevice) !=
+                        cudaSuccess) ||
       cudaMemset(md->m, 0, sizeof(float) * md->n_params) != cudaSuccess ||
       cudaMemset(md->v, 0, sizeof(float) * md->n_params) != cudaSuccess ||
       cudaMemset(md->grad, 0, sizeof(float) * md->n_params) != cudaSuccess || refresh_bf16(md, st) != PPR_OK ||
@@ -904,12 +995,49 @@ ppr_status ppr_model_train(ppr_model* md, const int32_t* train_src, int32_t n_sr
   ppr_query_opts qo;
   ppr_default_opts(&qo);
   qo.alpha = 0.2;
+  double* xl = nullptr;
+  double* mu_d = nullptr;
+  if (md->L > 0 && (cudaMalloc(&xl, sizeof(double) * n * kMaxB) != cudaSuccess ||
+                    cudaMalloc(&mu_d, sizeof(double) * kMaxB) != cudaSuccess)) {
+    cudaFree(lab); cudaFree(buf); cudaFree(xl);
+    set_error("out of device memory for correction labels");
+    return PPR_ERR_OOM;
+  }
+  std::vector<ppr_stats> pst(kMaxB);
   for (int32_t c0 = 0; c0 < n_src && s == PPR_OK; c0 += kMaxB) {
     const int nc = std::min<int32_t>(kMaxB, n_src - c0);
     s = query_hp(g, train_src + c0, nc, qo, buf, nullptr, nullptr, st);
-    if (s == PPR_OK) labels_kernel<<<sm_count() * 4, 256, 0, st>>>(n, nc, buf, g->d_new_of_old, lab, n_src, c0);
+    if (s != PPR_OK) break;
+    if (md->L == 0) {
+      labels_kernel<<<sm_count() * 4, 256, 0, st>>>(n, nc, buf, g->d_new_of_old, lab, n_src, c0);
+    } else {
+      // target: the distribution of the mass the zero-start solve still misses after L passes
+      ppr_query_opts qp = qo;
+      qp.max_sweeps = md->L;
+      qp.flags = PPR_FLAG_PARTIAL;
+      s = query_hp(g, train_src + c0, nc, qp, xl, nullptr, pst.data(), st);
+      if (s != PPR_OK) break;
+      double mu_h[kMaxB];
+      for (int c = 0; c < nc; ++c) mu_h[c] = pst[c].mass_deficit;
+      PPR_CUDA_TRY(cudaMemcpyAsync(mu_d, mu_h, sizeof(double) * nc, cudaMemcpyHostToDevice, st));
+      correction_labels_kernel<<<sm_count() * 4, 256, 0, st>>>(n, nc, buf, xl, mu_d, g->d_new_of_old, lab, n_src,
+                                                               c0);
+      PPR_CUDA_TRY(cudaStreamSynchronize(st));
+    }
   }
   cudaFree(buf);
+  if (xl) cudaFree(xl);
+  if (mu_d) cudaFree(mu_d);
+  if (s == PPR_OK && md->L > 0 && md->step == 0) {
+    mean_shape_kernel<<<sm_count() * 4, 256, 0, st>>>(n, n_src, lab, md->R, md->p + md->off_U);
+    std::vector<float> w3col(md->H, 0.f);
+    for (int h = 0; h < md->H; ++h)
+      cudaMemcpyAsync(md->p + md->off_W3 + (int64_t)h * md->R, &w3col[h], sizeof(float), cudaMemcpyHostToDevice, st);
+    const float one = 1.f;
+    cudaMemcpyAsync(md->p + md->off_b3, &one, sizeof(float), cudaMemcpyHostToDevice, st);
+    cudaStreamSynchronize(st);
+    s = refresh_bf16(md, st);
+  }
   const int nb = (n_src + kMaxB - 1) / kMaxB;
   std::vector<int> order(nb);
   std::iota(order.begin(), order.end(), 0);
@@ -933,13 +1061,14 @@ ppr_status ppr_model_train(ppr_model* md, const int32_t* train_src, int32_t n_sr
   return s;
 }
 
-// checkpoint: magic, version, n, F, H, R, seed, step, then parameters and both Adam moments
+// checkpoint: magic, version, n, F, H, R, seed, step, correction passes, then
+// parameters and both Adam moments
 ppr_status ppr_model_save(const ppr_model* md, const char* path) {
   clear_error();
   if (!md || !path) { set_error("model and path must be non-NULL"); return PPR_ERR_ARG; }
   FILE* fp = fopen(path, "wb");
   if (!fp) { set_error("cannot open %s for writing", path); return PPR_ERR_ARG; }
-  const int64_t hdr[8] = {0x4d525050, 1, md->g->n, md->F, md->H, md->R, (int64_t)md->seed, md->step};
+  const int64_t hdr[9] = {0x4d525050, 2, md->g->n, md->F, md->H, md->R, (int64_t)md->seed, md->step, md->L};
   std::vector<float> buf(md->n_params);
   bool ok = fwrite(hdr, sizeof(hdr), 1, fp) == 1;
   for (const float* src : {md->p, md->m, md->v}) {
@@ -958,8 +1087,8 @@ ppr_status ppr_model_load(ppr_graph* g, const char* path, ppr_model** out) {
   *out = nullptr;
   FILE* fp = fopen(path, "rb");
   if (!fp) { set_error("cannot open %s", path); return PPR_ERR_ARG; }
-  int64_t hdr[8];
-  if (fread(hdr, sizeof(hdr), 1, fp) != 1 || hdr[0] != 0x4d525050 || hdr[1] != 1 || hdr[2] != g->n) {
+  int64_t hdr[9];
+  if (fread(hdr, sizeof(hdr), 1, fp) != 1 || hdr[0] != 0x4d525050 || hdr[1] != 2 || hdr[2] != g->n) {
     fclose(fp);
     set_error("%s is not a model checkpoint for this graph", path);
     return PPR_ERR_ARG;
@@ -970,6 +1099,7 @@ ppr_status ppr_model_load(ppr_graph* g, const char* path, ppr_model** out) {
   o.hidden = (int32_t)hdr[4];
   o.rank = (int32_t)hdr[5];
   o.seed = (uint64_t)hdr[6];
+  o.correction_passes = (int32_t)hdr[8];
   ppr_model* md = nullptr;
   ppr_status s = ppr_model_create(g, &o, &md);
   if (s != PPR_OK) { fclose(fp); return s; }
