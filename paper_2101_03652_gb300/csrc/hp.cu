@@ -38,6 +38,7 @@
 
 #include "ppr_internal.cuh"
 #include "sweep_kernel.cuh"
+#include "epoch_kernel.cuh"
 
 namespace ppr {
 
@@ -332,6 +333,77 @@ static void launch_sweep(const SweepArgs& a, int grid, cudaStream_t st) {
   sweep_kernel<KT><<<grid, 256, 0, st>>>(a);
 }
 
+// Algorithm 3's epochs from the push state (r, pi): epoch i pushes, in full
+// synchronous passes, every node with r(v) > d_v lambda^(i/E) / m until the
+// residue sum is at most lambda^(i/E) or no node is active.
+template <int KT>
+static ppr_status run_epochs(ppr_graph* g, const ppr_graph::SweepPlan& plan, int grid, int grid_ew, int E,
+                             double lambda, double alpha, int max_sweeps, int ncols, u64* r, u64* pi, u64* ya,
+                             u64* yb, u64* ctr, u64* hpin, int& sweeps, std::vector<double>& rsum,
+                             int64_t& launches, float& ms_sweep, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st) {
+  const int64_t n = g->n, m = g->m;
+  EpochArgs ea;
+  ea.items = plan.d_items;
+  ea.n_items = plan.n_items_all;
+  ea.in_rp = g->d_in_rp;
+  ea.in_ci = g->d_in_ci;
+  ea.deg = g->d_deg;
+  ea.omega = g->d_omega;
+  ea.r = r;
+  ea.pi = pi;
+  ea.alpha64 = (u64)(alpha * 18446744073709551616.0);
+  ea.npieces = plan.d_npieces;
+  ea.heavy_acc = g->ws.heavy_acc.as<u64>();
+  ea.heavy_cnt = g->ws.heavy_cnt.as<unsigned int>();
+  ea.rsum = ctr;
+  ea.active = ctr + 64;
+  auto max_rsum = [&]() {
+    double mx = 0.0;
+    for (int c = 0; c < ncols; ++c) mx = std::max(mx, rsum[c]);
+    return mx;
+  };
+  for (int i = 1; i <= E; ++i) {
+    const double thr = std::pow(lambda, (double)i / (double)E);  // m r'_max
+    const u64 rmax_raw = (u64)std::max(1.0, std::floor(thr / (double)m * kFixOne));
+    if (max_rsum() <= thr) continue;
+    PPR_CUDA_TRY(cudaMemsetAsync(ctr + 64, 0, 8, st));
+    epoch_activate_kernel<KT><<<grid_ew, 256, 0, st>>>(n, g->d_deg, g->d_omega, r, rmax_raw, ya, ctr + 64);
+    ++launches;
+    PPR_CUDA_TRY(cudaMemcpyAsync(hpin, ctr + 64, 8, cudaMemcpyDeviceToHost, st));
+    PPR_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hpin[0] == 0) continue;  // a pass would push nothing: the epoch ends
+    ea.rmax_raw = rmax_raw;
+    while (true) {
+      if (sweeps >= max_sweeps) {
+        set_error("sweep limit %d reached in the epochs", max_sweeps);
+        return PPR_ERR_NOT_CONVERGED;
+      }
+      PPR_CUDA_TRY(cudaMemsetAsync(ctr, 0, 8 * 128, st));
+      ea.y_in = ya;
+      ea.y_out = yb;
+      PPR_CUDA_TRY(cudaEventRecord(e0, st));
+      epoch_sweep_kernel<KT><<<grid, 256, 0, st>>>(ea);
+      PPR_CUDA_TRY(cudaEventRecord(e1, st));
+      PPR_CUDA_TRY(cudaGetLastError());
+      ++launches;
+      ++sweeps;
+      std::swap(ya, yb);
+      PPR_CUDA_TRY(cudaMemcpyAsync(hpin, ctr, 8 * 128, cudaMemcpyDeviceToHost, st));
+      PPR_CUDA_TRY(cudaStreamSynchronize(st));
+      float a = 0.f;
+      cudaEventElapsedTime(&a, e0, e1);
+      ms_sweep += a;
+      u64 act = 0;
+      for (int c = 0; c < ncols; ++c) {
+        rsum[c] = (double)hpin[c] / kFixOne;
+        act += hpin[64 + c];
+      }
+      if (max_rsum() <= thr || act == 0) break;
+    }
+  }
+  return PPR_OK;
+}
+
 template <int KT>
 static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query_opts& o, double* out_pi,
                          double* out_r, ppr_stats* stats, cudaStream_t st) {
@@ -379,7 +451,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
   bool fresh_heavy = ws.heavy_acc.bytes < acc_bytes || ws.heavy_cnt.bytes < cnt_bytes;
   PPR_TRY(ws.heavy_acc.ensure(acc_bytes));
   PPR_TRY(ws.heavy_cnt.ensure(cnt_bytes));
-  PPR_TRY(ws.counters.ensure(8192));
+  PPR_TRY(ws.counters.ensure(16384));
   PPR_TRY(ws.resid.ensure((size_t)(max_sweeps + 1) * 64 * 8));
 
   if (stage_bytes) PPR_TRY(ws.stage.ensure(stage_bytes));
@@ -516,6 +588,28 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
     bool need_dense = !all_done;
     if (!need_dense) {
       for (int c = 0; c < ncols; ++c) bound[c] = rsum[c];
+    } else if (o.epoch_num > 0) {
+      // Algorithm 3's epochs (thresholded passes) instead of push-every-node passes
+      if (!have_state) {
+        PPR_CUDA_TRY(cudaMemsetAsync(r, 0, cells * 8, st));
+        PPR_CUDA_TRY(cudaMemsetAsync(pi, 0, cells * 8, st));
+        PPR_CUDA_TRY(cudaMemcpyAsync(d_src, src_new, sizeof(src_new), cudaMemcpyHostToDevice, st));
+        init_sources_kernel<KT><<<1, 64, 0, st>>>(d_src, ncols, r, ws.stamp.as<uint32_t>(), ++g->stamp_epoch,
+                                                  ws.front_a.as<uint32_t>());
+        ++launches;
+        for (int c = 0; c < ncols; ++c) rsum[c] = 1.0;
+      }
+      for (int c = 0; c < ncols; ++c) r0[c] = rsum[c];
+      status = run_epochs<KT>(g, plan, sweep_grid, grid_ew, o.epoch_num, lambda, alpha, max_sweeps, ncols, r, pi, za,
+                              zb, counters + 1024, hpin, sweeps, rsum, launches, ms_sweep, es0, es1, st);
+      if (status != PPR_OK) break;
+      sweep_launches += sweeps;
+      // each pass rounds d shares per node by at most half a unit each
+      const double slack = (double)sweeps * (double)m * 0.5 / kFixOne;
+      for (int c = 0; c < ncols; ++c) bound[c] = rsum[c] + slack;
+      xfinal = pi;
+      if (out_r)
+        output_kernel<KT><<<grid_ew, 256, 0, st>>>(n, g->d_new_of_old, r, ncols, t0, out_r_dev), ++launches;
     } else {
       if (warm) {
         // x0 from the model; its residual norm is measured by the first pass

@@ -183,3 +183,24 @@ def test_rmat20_bench_configuration(P, rmat20):
         ref, _, _ = O.powerpush(og, int(src[i]), ALPHA, LAM)
         assert np.abs(pi[i] - ref).sum() <= 2 * LAM
     assert np.all(pi >= 0)
+
+
+@pytest.mark.parametrize("k_tile", [1, 8])
+def test_algorithm3_epochs_against_oracle(P, c0, c0_ref, k_tile):
+    """epoch_num = 8: Algorithm 3's thresholded epochs (r'_max = lambda^(i/8)/m)."""
+    rp, ci, src = c0
+    pi, st = run(P, rp, ci, src, k_tile=k_tile, epoch_num=8)
+    for i, s in enumerate(src):
+        assert np.abs(pi[i] - c0_ref[int(s)]).sum() <= 2 * LAM
+    check_bound_and_mass(st)
+    pi_all, st_all = run(P, rp, ci, src, k_tile=k_tile)
+    # thresholded synchronous passes converge more slowly per pass than pushing every node
+    assert st[0]["sweeps"] >= st_all[0]["sweeps"]
+
+
+def test_algorithm3_epochs_from_zero_start(P, c0, c0_ref):
+    rp, ci, src = c0
+    pi, st = run(P, rp, ci, src[:4], epoch_num=4, switch_edges=0)
+    for i, s in enumerate(src[:4]):
+        assert np.abs(pi[i] - c0_ref[int(s)]).sum() <= 2 * LAM
+    check_bound_and_mass(st)
