@@ -342,17 +342,127 @@ def warm_start_comparison(P, g, n, k, kt, out, flush, rank, train_n=4096, held_n
             "speedup": res["warm"]["queries_per_s"] / res["plain"]["queries_per_s"]}
 
 
+def run_serve(args):
+    """Serving: requests (one source each) arrive as a Poisson stream; a single
+    GPU server takes up to 32 queued requests per batch, admitted against free
+    device memory (ppr_query_state_bytes), and answers them with the plain
+    zero start or the learned warm start.  Latency = completion - arrival;
+    the clock is virtual and advances by each batch's measured GPU time."""
+    import collections
+    import numpy as np
+    import torch
+    import ppr_inputs as gen
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2101_03652_gb300 as P
+    torch.cuda.set_device(0)
+    t = time.perf_counter()
+    rp, ci = gen.rmat(args.serve_scale, args.serve_ef, seed=1)
+    gen_s = time.perf_counter() - t
+    n, m = len(rp) - 1, len(ci)
+    t = time.perf_counter()
+    g = P.Graph(rp, ci)
+    load_s = time.perf_counter() - t
+    del rp, ci
+    kmax = 32
+    out = torch.empty((kmax, n), dtype=torch.float64, device="cuda")
+    free0 = torch.cuda.mem_get_info()[0]
+
+    def run_batch(srcs, model):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, st = g.query(srcs, P.PPR_HP, out_pi=out[:len(srcs)], lam=LAMBDA, warm_start=model)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, st[0]["sweeps"]
+
+    def admit(k):
+        budget = torch.cuda.mem_get_info()[0] + g.state_bytes(kmax)  # workspace is reused once held
+        while k > 1 and g.state_bytes(k) > budget:
+            k //= 2
+        return k
+
+    def peak(model, seed, batches=3):
+        srcs = gen.sources(n, kmax * batches, seed=seed)
+        run_batch(srcs[:kmax], model)  # warm-up
+        tot, sw = 0.0, []
+        for b in range(batches):
+            d, s = run_batch(srcs[b * kmax:(b + 1) * kmax], model)
+            tot += d
+            sw.append(s)
+        return kmax * batches / tot, float(np.mean(sw))
+
+    plain_qps, plain_passes = peak(None, seed=6)
+    t = time.perf_counter()
+    model = P.Model(g, seed=0x5EED, correction_passes=8)
+    train = gen.sources(n, args.serve_train, seed=7)
+    model.train(train, epochs=1, lr=2e-3, shuffle_seed=1)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t
+    warm_qps, warm_passes = peak(model, seed=6)
+
+    def simulate(rate, model, seed):
+        rng = np.random.default_rng(seed)
+        nreq = args.serve_requests
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
+        srcs = gen.sources(n, nreq, seed=seed)
+        queue = collections.deque()
+        lat = np.zeros(nreq)
+        t_free, i, done = 0.0, 0, 0
+        while done < nreq:
+            while i < nreq and arrivals[i] <= t_free:
+                queue.append(i)
+                i += 1
+            if not queue:
+                t_free = arrivals[i]
+                continue
+            k = admit(min(kmax, len(queue)))
+            batch = [queue.popleft() for _ in range(k)]
+            d, _ = run_batch(srcs[batch], model)
+            t_free += d
+            for j in batch:
+                lat[j] = t_free - arrivals[j]
+            done += k
+        span = t_free - arrivals[0]
+        return {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "queries_per_s": nreq / span}
+
+    load = []
+    for frac in (0.5, 0.8):
+        rate = frac * plain_qps
+        load.append({"rate_frac_of_plain_peak": frac, "arrival_qps": rate,
+                     "plain": simulate(rate, None, seed=8), "warm": simulate(rate, model, seed=8)})
+    print(json.dumps({
+        "metric": "serving: p50/p99 latency and queries/s at l1<=1e-8, learned warm start vs plain batched",
+        "workload": "rmat%d-serve" % args.serve_scale, "data": "synthetic",
+        "graph": {"scale": args.serve_scale, "edge_factor": args.serve_ef, "n": n, "m": m},
+        "batch": kmax, "requests": args.serve_requests, "train_sources": args.serve_train,
+        "setup_s": {"generate": gen_s, "load": load_s, "train_incl_labels": train_s},
+        "free_hbm_gb_after_load": free0 / 1e9,
+        "peak": {"plain": {"queries_per_s": plain_qps, "passes": plain_passes},
+                 "warm": {"queries_per_s": warm_qps, "passes": warm_passes}},
+        "load": load}))
+    model.close()
+    g.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat20-k64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rmat20-k64", choices=sorted(WORKLOADS) + ["serve"])
     ap.add_argument("--skip-cpu", action="store_true", help="omit the oracle CPU baseline")
     ap.add_argument("--skip-warm", action="store_true", help="omit the learned warm-start comparison")
+    ap.add_argument("--serve-scale", type=int, default=25, help="R-MAT scale of the serving workload")
+    ap.add_argument("--serve-ef", type=int, default=32)
+    ap.add_argument("--serve-train", type=int, default=2048)
+    ap.add_argument("--serve-requests", type=int, default=512)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.workload == "serve":
+        run_serve(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -152,6 +152,12 @@ ppr_status ppr_sssp_query(ppr_graph* g, const int32_t* src, int32_t k, ppr_mode 
 ppr_status ppr_sssp_query_noalloc(ppr_graph* g, const int32_t* src, int32_t k, double alpha, double lambda,
                                   double* out_pi, int32_t* out_sweeps, void* cuda_stream);
 
+/* Device bytes the workspace of a high-precision query of k sources needs
+ * (k_tile as in ppr_query_opts, 0 = auto); the library reuses the workspace
+ * across calls, so a server can admit a batch when this fits in free memory
+ * plus what the graph already holds.  -1 on bad arguments. */
+int64_t ppr_query_state_bytes(const ppr_graph* g, int32_t k, int32_t k_tile);
+
 /* Release the graph and every device buffer it owns; NULL is allowed. */
 void ppr_free(ppr_graph* g);
 

@@ -96,6 +96,7 @@ SIGNATURES = {
     "ppr_last_error": (ctypes.c_char_p, []),
     "ppr_graph_n": (ctypes.c_int64, [_P]),
     "ppr_graph_m": (ctypes.c_int64, [_P]),
+    "ppr_query_state_bytes": (ctypes.c_int64, [_P, ctypes.c_int32, ctypes.c_int32]),
     "ppr_model_default_opts": (None, [ctypes.POINTER(ppr_model_opts)]),
     "ppr_model_create": (ctypes.c_int, [_P, ctypes.POINTER(ppr_model_opts), ctypes.POINTER(_P)]),
     "ppr_model_train": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_uint64,
@@ -225,6 +226,10 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+    def state_bytes(self, k: int, k_tile: int = 0) -> int:
+        """Device workspace of a high-precision query of k sources."""
+        return load_library().ppr_query_state_bytes(self.handle, k, k_tile)
 
     def query(self, src, mode: int = PPR_HP, out_pi=None, out_r=None, out_walk_counts=None, stream=None,
               warm_start=None, **opts):

@@ -13,6 +13,11 @@ extern "C" {
 
 const char* ppr_last_error(void) { return last_error_cstr(); }
 
+int64_t ppr_query_state_bytes(const ppr_graph* g, int32_t k, int32_t k_tile) {
+  if (!g || k < 1 || k_tile < 0 || k_tile > 64 || (k_tile & (k_tile - 1))) return -1;
+  return hp_state_bytes(g, k, k_tile);
+}
+
 ppr_status ppr_sssp_query(ppr_graph* g, const int32_t* src, int32_t k, ppr_mode mode, const ppr_query_opts* opts,
                           double* out_pi, double* out_r, uint32_t* out_walk_counts, ppr_stats* stats,
                           void* cuda_stream) {

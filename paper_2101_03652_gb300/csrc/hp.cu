@@ -783,6 +783,19 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
   return status;
 }
 
+// device bytes a high-precision query of k sources allocates (workspace for one
+// tile), as used by the admission check of run_hp (host staging excluded)
+int64_t hp_state_bytes(const ppr_graph* g, int32_t k, int32_t kt) {
+  if (kt == 0) {
+    kt = 1;
+    while (kt < k && kt < 64) kt <<= 1;
+  }
+  const size_t cells = (size_t)g->n * kt;
+  const int max_sweeps = 4 * 83 + 64;
+  return (int64_t)(4 * cells * 8 + cells * 4 * 4 + cells * 16 + (size_t)g->m * kt / kPushChunk * 8 +
+                   (size_t)max_sweeps * kt * 8);
+}
+
 ppr_status query_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query_opts& o, double* out_pi,
                     double* out_r, ppr_stats* stats, cudaStream_t st) {
   int kt = o.k_tile;

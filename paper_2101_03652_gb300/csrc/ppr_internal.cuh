@@ -109,6 +109,7 @@ int sm_count();
 ppr_status warm_start_tile(const void* model, ppr_graph* g, const int32_t* src_new, int ncols, int kt, double alpha,
                            unsigned long long* z0, cudaStream_t st);
 int warm_correction_passes(const void* model);
+int64_t hp_state_bytes(const ppr_graph* g, int32_t k, int32_t kt);
 ppr_status warm_correct_tile(const void* model, ppr_graph* g, const int32_t* src_new, int ncols, int kt, double alpha,
                              const unsigned long long* x, const unsigned long long* mass, unsigned long long* z,
                              cudaStream_t st);

@@ -973,21 +973,33 @@ ppr_status ppr_model_train(ppr_model* md, const int32_t* train_src, int32_t n_sr
   for (int32_t i = 0; i < n_src; ++i)
     if (train_src[i] < 0 || train_src[i] >= n) { set_error("training source out of range"); return PPR_ERR_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
-  // exact labels from the plain high-precision method, stored [n][n_src] in FP32
+  // Exact labels from the plain high-precision method, [n][chunk] FP32.  When
+  // labels for every source do not fit in half of the free device memory, the
+  // sources are taken in chunks whose labels are regenerated every epoch.
+  size_t free_b = 0, total_b = 0;
+  PPR_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  // label queries use the widest tile whose workspace takes at most 30 % of free memory
+  int kt_label = kMaxB;
+  while (kt_label > 1 && (double)hp_state_bytes(g, kMaxB, kt_label) > 0.3 * (double)free_b) kt_label /= 2;
+  const size_t fixed = 2 * sizeof(double) * n * kMaxB + (size_t)hp_state_bytes(g, kMaxB, kt_label) +
+                       ((size_t)1 << 30);
+  if (free_b < fixed + sizeof(float) * (size_t)n * kMaxB) {
+    set_error("admission refused: training needs at least %zu bytes, %zu free", fixed, free_b);
+    return PPR_ERR_ADMIT;
+  }
+  int32_t chunk = n_src;
+  if (sizeof(float) * (size_t)n * n_src > (free_b - fixed) / 2)
+    chunk = std::max<int32_t>(kMaxB, (int32_t)(((free_b - fixed) / 2 / (sizeof(float) * (size_t)n)) / kMaxB * kMaxB));
+  chunk = std::min(chunk, n_src);
   float* lab = nullptr;
   double* buf = nullptr;
-  const size_t lab_bytes = sizeof(float) * (size_t)n * n_src;
-  {
-    size_t free_b = 0, total_b = 0;
-    PPR_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-    if (lab_bytes + sizeof(double) * n * kMaxB + ((size_t)1 << 30) > free_b) {
-      set_error("admission refused: training labels need %zu bytes, %zu free", lab_bytes, free_b);
-      return PPR_ERR_ADMIT;
-    }
-  }
-  PPR_CUDA_TRY(cudaMalloc(&lab, lab_bytes));
-  if (cudaMalloc(&buf, sizeof(double) * n * kMaxB) != cudaSuccess) {
-    cudaFree(lab);
+  double* xl = nullptr;
+  double* mu_d = nullptr;
+  PPR_CUDA_TRY(cudaMalloc(&lab, sizeof(float) * (size_t)n * chunk));
+  if (cudaMalloc(&buf, sizeof(double) * n * kMaxB) != cudaSuccess ||
+      (md->L > 0 && (cudaMalloc(&xl, sizeof(double) * n * kMaxB) != cudaSuccess ||
+                     cudaMalloc(&mu_d, sizeof(double) * kMaxB) != cudaSuccess))) {
+    cudaFree(lab); cudaFree(buf); cudaFree(xl);
     set_error("out of device memory for label generation");
     return PPR_ERR_OOM;
   }
@@ -995,67 +1007,78 @@ ppr_status ppr_model_train(ppr_model* md, const int32_t* train_src, int32_t n_sr
   ppr_query_opts qo;
   ppr_default_opts(&qo);
   qo.alpha = 0.2;
-  double* xl = nullptr;
-  double* mu_d = nullptr;
-  if (md->L > 0 && (cudaMalloc(&xl, sizeof(double) * n * kMaxB) != cudaSuccess ||
-                    cudaMalloc(&mu_d, sizeof(double) * kMaxB) != cudaSuccess)) {
-    cudaFree(lab); cudaFree(buf); cudaFree(xl);
-    set_error("out of device memory for correction labels");
-    return PPR_ERR_OOM;
-  }
+  qo.k_tile = kt_label;
   std::vector<ppr_stats> pst(kMaxB);
-  for (int32_t c0 = 0; c0 < n_src && s == PPR_OK; c0 += kMaxB) {
-    const int nc = std::min<int32_t>(kMaxB, n_src - c0);
-    s = query_hp(g, train_src + c0, nc, qo, buf, nullptr, nullptr, st);
-    if (s != PPR_OK) break;
-    if (md->L == 0) {
-      labels_kernel<<<sm_count() * 4, 256, 0, st>>>(n, nc, buf, g->d_new_of_old, lab, n_src, c0);
-    } else {
-      // target: the distribution of the mass the zero-start solve still misses after L passes
-      ppr_query_opts qp = qo;
-      qp.max_sweeps = md->L;
-      qp.flags = PPR_FLAG_PARTIAL;
-      s = query_hp(g, train_src + c0, nc, qp, xl, nullptr, pst.data(), st);
-      if (s != PPR_OK) break;
-      double mu_h[kMaxB];
-      for (int c = 0; c < nc; ++c) mu_h[c] = pst[c].mass_deficit;
-      PPR_CUDA_TRY(cudaMemcpyAsync(mu_d, mu_h, sizeof(double) * nc, cudaMemcpyHostToDevice, st));
-      correction_labels_kernel<<<sm_count() * 4, 256, 0, st>>>(n, nc, buf, xl, mu_d, g->d_new_of_old, lab, n_src,
-                                                               c0);
-      PPR_CUDA_TRY(cudaStreamSynchronize(st));
+  // labels for sources [c0, c0 + cnt) into columns [0, cnt) of lab (ld = chunk)
+  auto make_labels = [&](int32_t c0, int32_t cnt) -> ppr_status {
+    for (int32_t b = 0; b < cnt; b += kMaxB) {
+      const int nc = std::min<int32_t>(kMaxB, cnt - b);
+      PPR_TRY(query_hp(g, train_src + c0 + b, nc, qo, buf, nullptr, nullptr, st));
+      if (md->L == 0) {
+        labels_kernel<<<sm_count() * 4, 256, 0, st>>>(n, nc, buf, g->d_new_of_old, lab, chunk, b);
+      } else {
+        // target: the distribution of the mass the zero-start solve still misses after L passes
+        ppr_query_opts qp = qo;
+        qp.max_sweeps = md->L;
+        qp.flags = PPR_FLAG_PARTIAL;
+        PPR_TRY(query_hp(g, train_src + c0 + b, nc, qp, xl, nullptr, pst.data(), st));
+        double mu_h[kMaxB];
+        for (int c = 0; c < nc; ++c) mu_h[c] = pst[c].mass_deficit;
+        PPR_CUDA_TRY(cudaMemcpyAsync(mu_d, mu_h, sizeof(double) * nc, cudaMemcpyHostToDevice, st));
+        correction_labels_kernel<<<sm_count() * 4, 256, 0, st>>>(n, nc, buf, xl, mu_d, g->d_new_of_old, lab, chunk,
+                                                                 b);
+        PPR_CUDA_TRY(cudaStreamSynchronize(st));
+      }
     }
+    return PPR_OK;
+  };
+  auto shape_init = [&](int32_t cnt) -> ppr_status {
+    mean_shape_kernel<<<sm_count() * 4, 256, 0, st>>>(n, cnt, lab, md->R, md->p + md->off_U);
+    std::vector<float> zero(md->H, 0.f);
+    for (int h = 0; h < md->H; ++h)
+      PPR_CUDA_TRY(cudaMemcpyAsync(md->p + md->off_W3 + (int64_t)h * md->R, &zero[h], sizeof(float),
+                                   cudaMemcpyHostToDevice, st));
+    const float one = 1.f;
+    PPR_CUDA_TRY(cudaMemcpyAsync(md->p + md->off_b3, &one, sizeof(float), cudaMemcpyHostToDevice, st));
+    PPR_CUDA_TRY(cudaStreamSynchronize(st));
+    return refresh_bf16(md, st);
+  };
+  const int nchunks = (n_src + chunk - 1) / chunk;
+  std::vector<int> chunk_order(nchunks);
+  std::iota(chunk_order.begin(), chunk_order.end(), 0);
+  bool labels_ready = false;
+  for (int ep = 0; (ep < epochs || (ep == 0 && md->L > 0 && md->step == 0)) && s == PPR_OK; ++ep) {
+    std::mt19937_64 rng(shuffle_seed + (uint64_t)ep);
+    std::shuffle(chunk_order.begin(), chunk_order.end(), rng);
+    double tot = 0.0;
+    for (int ci = 0; ci < nchunks && s == PPR_OK; ++ci) {
+      const int32_t c0 = chunk_order[ci] * chunk;
+      const int32_t cnt = std::min<int32_t>(chunk, n_src - c0);
+      if (!labels_ready) s = make_labels(c0, cnt);
+      if (s != PPR_OK) break;
+      if (nchunks == 1) labels_ready = true;
+      // a correction model starts at the mean target of the first labels it sees
+      if (md->L > 0 && md->step == 0) s = shape_init(cnt);
+      if (s != PPR_OK || ep >= epochs) break;
+      const int nb = (cnt + kMaxB - 1) / kMaxB;
+      std::vector<int> order(nb);
+      std::iota(order.begin(), order.end(), 0);
+      std::shuffle(order.begin(), order.end(), rng);
+      for (int bi = 0; bi < nb && s == PPR_OK; ++bi) {
+        const int b0 = order[bi] * kMaxB;
+        const int nc = std::min<int32_t>(kMaxB, cnt - b0);
+        std::vector<int32_t> s_new(nc);
+        for (int i = 0; i < nc; ++i) s_new[i] = g->h_new_of_old[train_src[c0 + b0 + i]];
+        double l = 0.0;
+        s = model_step(md, s_new.data(), nc, lab + b0, chunk, 0.2, lr, &l, st);
+        tot += l * nc;
+      }
+    }
+    if (loss_per_epoch && ep < epochs) loss_per_epoch[ep] = (float)(tot / n_src);
   }
   cudaFree(buf);
   if (xl) cudaFree(xl);
   if (mu_d) cudaFree(mu_d);
-  if (s == PPR_OK && md->L > 0 && md->step == 0) {
-    mean_shape_kernel<<<sm_count() * 4, 256, 0, st>>>(n, n_src, lab, md->R, md->p + md->off_U);
-    std::vector<float> w3col(md->H, 0.f);
-    for (int h = 0; h < md->H; ++h)
-      cudaMemcpyAsync(md->p + md->off_W3 + (int64_t)h * md->R, &w3col[h], sizeof(float), cudaMemcpyHostToDevice, st);
-    const float one = 1.f;
-    cudaMemcpyAsync(md->p + md->off_b3, &one, sizeof(float), cudaMemcpyHostToDevice, st);
-    cudaStreamSynchronize(st);
-    s = refresh_bf16(md, st);
-  }
-  const int nb = (n_src + kMaxB - 1) / kMaxB;
-  std::vector<int> order(nb);
-  std::iota(order.begin(), order.end(), 0);
-  for (int ep = 0; ep < epochs && s == PPR_OK; ++ep) {
-    std::mt19937_64 rng(shuffle_seed + (uint64_t)ep);
-    std::shuffle(order.begin(), order.end(), rng);
-    double tot = 0.0;
-    for (int bi = 0; bi < nb && s == PPR_OK; ++bi) {
-      const int c0 = order[bi] * kMaxB;
-      const int nc = std::min<int32_t>(kMaxB, n_src - c0);
-      std::vector<int32_t> s_new(nc);
-      for (int i = 0; i < nc; ++i) s_new[i] = g->h_new_of_old[train_src[c0 + i]];
-      double l = 0.0;
-      s = model_step(md, s_new.data(), nc, lab + c0, n_src, 0.2, lr, &l, st);
-      tot += l * nc;
-    }
-    if (loss_per_epoch) loss_per_epoch[ep] = (float)(tot / n_src);
-  }
   cudaStreamSynchronize(st);
   cudaFree(lab);
   return s;
