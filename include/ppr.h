@@ -158,6 +158,20 @@ ppr_status ppr_sssp_query_noalloc(ppr_graph* g, const int32_t* src, int32_t k, d
  * plus what the graph already holds.  -1 on bad arguments. */
 int64_t ppr_query_state_bytes(const ppr_graph* g, int32_t k, int32_t k_tile);
 
+/*
+ * Measure, on a calibration batch src[k], every tile width up to the smallest
+ * power of two >= k (at most 64) combined with queue->sweep switch thresholds
+ * of {0, 0.002, 0.02, 0.1} x m x k_tile frontier edges (Algorithm 3 fixes
+ * scanThreshold = n/4 for a CPU), each timed with CUDA events on the stream.
+ * The fastest setting is written to *best (from *base, NULL = defaults),
+ * its time to *best_ms (optional), and remembered in the graph for later HP
+ * calls with k_tile = 0 / switch_edges = -1 and a k of the same power-of-two
+ * bucket.  out_pi: device k x n float64 scratch for the calibration answers.
+ * Widths whose workspace does not fit are skipped.  Errors as ppr_sssp_query.
+ */
+ppr_status ppr_autotune(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query_opts* base, double* out_pi,
+                        ppr_query_opts* best, double* best_ms, void* cuda_stream);
+
 /* Release the graph and every device buffer it owns; NULL is allowed. */
 void ppr_free(ppr_graph* g);
 

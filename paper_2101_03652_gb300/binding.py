@@ -97,6 +97,8 @@ SIGNATURES = {
     "ppr_graph_n": (ctypes.c_int64, [_P]),
     "ppr_graph_m": (ctypes.c_int64, [_P]),
     "ppr_query_state_bytes": (ctypes.c_int64, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "ppr_autotune": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(ppr_query_opts), _P,
+                                    ctypes.POINTER(ppr_query_opts), ctypes.POINTER(ctypes.c_double), _P]),
     "ppr_model_default_opts": (None, [ctypes.POINTER(ppr_model_opts)]),
     "ppr_model_create": (ctypes.c_int, [_P, ctypes.POINTER(ppr_model_opts), ctypes.POINTER(_P)]),
     "ppr_model_train": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_uint64,
@@ -226,6 +228,19 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+    def autotune(self, src, stream=None, **opts):
+        """Time tile widths and switch thresholds on src; returns (k_tile,
+        switch_edges, ms) of the fastest, which later auto calls use."""
+        import torch
+        s = np.ascontiguousarray(src, dtype=np.int32)
+        out = torch.empty((len(s), self.n), dtype=torch.float64, device="cuda")
+        base = ppr_default_opts(**opts)
+        best = ppr_query_opts()
+        ms = ctypes.c_double()
+        _check(load_library().ppr_autotune(self.handle, s.ctypes.data, len(s), ctypes.byref(base), _ptr(out),
+                                           ctypes.byref(best), ctypes.byref(ms), _stream(stream)))
+        return best.k_tile, best.switch_edges, ms.value
 
     def state_bytes(self, k: int, k_tile: int = 0) -> int:
         """Device workspace of a high-precision query of k sources."""

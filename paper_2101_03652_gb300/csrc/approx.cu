@@ -356,60 +356,73 @@ struct WalkArgs {
   int32_t col0;          // source index of the tile's first column
 };
 
+// Each thread runs kWalksPerThread consecutive walk ids, so the start node
+// advances monotonically (one binary search per thread) and a warp waits for
+// the longest of its threads' walk *sums* rather than of single walks.  A
+// thread merges consecutive endpoints at the same node before its atomics.
+constexpr int kWalksPerThread = 16;
+
 template <int KT>
 __global__ void __launch_bounds__(256) walk_kernel(WalkArgs a) {
   const int c = blockIdx.y;
   const int64_t* offs = a.offs + (size_t)c * (a.n + 1);
   const int64_t total = offs[a.n];
-  const int64_t w0 = (int64_t)blockIdx.x * blockDim.x;
-  if (w0 >= total) return;
-  // narrow the search range to the start nodes of this block's walks
-  __shared__ int64_t range[2];
-  if (threadIdx.x < 2) {
-    const int64_t target = threadIdx.x == 0 ? w0 : min(w0 + (int64_t)blockDim.x - 1, total - 1);
-    int64_t lo = 0, hi = a.n - 1;  // last o with offs[o] <= target
-    while (lo < hi) {
-      const int64_t mid = (lo + hi + 1) >> 1;
-      if (offs[mid] <= target) lo = mid; else hi = mid - 1;
-    }
-    range[threadIdx.x] = lo;
-  }
-  __syncthreads();
-  const int64_t w = w0 + threadIdx.x;
+  const int64_t w_begin = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kWalksPerThread;
   u64 moves = 0;
-  if (w < total) {
-    int64_t lo = range[0], hi = range[1];
+  if (w_begin < total) {
+    const int64_t w_end = min(w_begin + (int64_t)kWalksPerThread, total);
+    int64_t lo = 0, hi = a.n - 1;  // last o with offs[o] <= w_begin
     while (lo < hi) {
       const int64_t mid = (lo + hi + 1) >> 1;
-      if (offs[mid] <= w) lo = mid; else hi = mid - 1;
+      if (offs[mid] <= w_begin) lo = mid; else hi = mid - 1;
     }
-    const int64_t o = lo;
-    const int32_t v = a.new_of_old[o];
-    const double rv = (double)a.r[(size_t)v * KT + c];
-    const double inc = rv / (double)(offs[o + 1] - offs[o]);
-    int32_t cur = v;
-    uint4 words = make_uint4(0, 0, 0, 0);
-    int32_t t = 0;
-    bool ok = true;
-    for (;;) {
-      if ((t & 1) == 0)
-        words = philox4x32_10(make_uint4((uint32_t)w, (uint32_t)((u64)w >> 32), (uint32_t)(t >> 1),
-                                         (uint32_t)(a.col0 + c)),
-                              a.key0, a.key1);
-      const uint32_t stopw = (t & 1) ? words.z : words.x;
-      const uint32_t movew = (t & 1) ? words.w : words.y;
-      if (stopw < a.stop_below) break;
-      if (t >= a.max_steps) { ok = false; break; }
-      const int32_t d = __ldg(&a.deg[cur]);
-      cur = __ldg(&a.out_ci[__ldg(&a.out_rp[cur]) + (int32_t)__umulhi(movew, (uint32_t)d)]);
-      ++t;
+    int64_t o = lo;
+    int32_t pend_u = -1;
+    unsigned pend_n = 0;
+    double pend_est = 0.0;
+    for (int64_t w = w_begin; w < w_end; ++w) {
+      while (offs[o + 1] <= w) ++o;
+      const int32_t v = a.new_of_old[o];
+      const double rv = (double)a.r[(size_t)v * KT + c];
+      const double inc = rv / (double)(offs[o + 1] - offs[o]);
+      int32_t cur = v;
+      uint4 words = make_uint4(0, 0, 0, 0);
+      int32_t t = 0;
+      bool ok = true;
+      for (;;) {
+        if ((t & 1) == 0)
+          words = philox4x32_10(make_uint4((uint32_t)w, (uint32_t)((u64)w >> 32), (uint32_t)(t >> 1),
+                                           (uint32_t)(a.col0 + c)),
+                                a.key0, a.key1);
+        const uint32_t stopw = (t & 1) ? words.z : words.x;
+        const uint32_t movew = (t & 1) ? words.w : words.y;
+        if (stopw < a.stop_below) break;
+        if (t >= a.max_steps) { ok = false; break; }
+        const int32_t e0 = __ldg(&a.out_rp[cur]);
+        const int32_t d = __ldg(&a.out_rp[cur + 1]) - e0;
+        cur = __ldg(&a.out_ci[e0 + (int32_t)__umulhi(movew, (uint32_t)d)]);
+        ++t;
+      }
+      if (!ok) {
+        atomicExch(a.status, 1);
+        continue;
+      }
+      moves += (u64)t;
+      if (cur != pend_u) {
+        if (pend_n) {
+          atomicAdd(&a.counts[(size_t)pend_u * KT + c], pend_n);
+          atomicAdd(&a.est[(size_t)pend_u * KT + c], pend_est);
+        }
+        pend_u = cur;
+        pend_n = 0;
+        pend_est = 0.0;
+      }
+      pend_n += 1;
+      pend_est += inc;
     }
-    if (ok) {
-      atomicAdd(&a.counts[(size_t)cur * KT + c], 1u);
-      atomicAdd(&a.est[(size_t)cur * KT + c], inc);
-      moves = (u64)t;
-    } else {
-      atomicExch(a.status, 1);
+    if (pend_n) {
+      atomicAdd(&a.counts[(size_t)pend_u * KT + c], pend_n);
+      atomicAdd(&a.est[(size_t)pend_u * KT + c], pend_est);
     }
   }
 #pragma unroll
@@ -616,7 +629,7 @@ static ppr_status run_approx(ppr_graph* g, const int32_t* src, int32_t k, const 
         wa.stop_below = (uint32_t)std::floor(alpha * 4294967296.0);
         wa.max_steps = max_steps;
         wa.col0 = t0;
-        dim3 gw((unsigned)((maxw + 255) / 256), ncols);
+        dim3 gw((unsigned)((maxw + 256LL * kWalksPerThread - 1) / (256LL * kWalksPerThread)), ncols);
         walk_kernel<KT><<<gw, 256, 0, st>>>(wa);
         ++launches;
         PPR_CUDA_TRY(cudaGetLastError());

@@ -1,0 +1,80 @@
+// Autotuner for the tile width and the queue->sweep switch threshold.
+//
+// The paper fixes scanThreshold = n/4 for its CPU (Algorithm 3), a cache
+// heuristic.  On the GPU the right switch point and the number of sources to
+// solve together depend on the graph and on k, so both are measured: the
+// calibration batch is answered with each candidate setting, timed with CUDA
+// events on the caller's stream, and the fastest setting is kept in the graph
+// for later calls with k_tile = 0 / switch_edges = -1 and a similar k.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "ppr_internal.cuh"
+
+using namespace ppr;
+
+namespace ppr {
+int tune_bucket(int32_t k) {
+  int b = 0;
+  while ((1 << b) < k && b < 6) ++b;
+  return b;  // k -> ceil(log2 k), capped at 64 sources
+}
+}  // namespace ppr
+
+extern "C" ppr_status ppr_autotune(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query_opts* base,
+                                   double* out_pi, ppr_query_opts* best, double* best_ms, void* cuda_stream) {
+  clear_error();
+  if (!g || !src || k < 1 || !out_pi || !best) {
+    set_error("autotune needs a graph, k >= 1 calibration sources, out_pi and best");
+    return PPR_ERR_ARG;
+  }
+  ppr_query_opts o;
+  if (base) o = *base; else ppr_default_opts(&o);
+  o.warm_start = nullptr;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  std::vector<int> kts;
+  for (int kt = 1; kt <= 64; kt <<= 1) {
+    kts.push_back(kt);
+    if (kt >= k) break;
+  }
+  const double fracs[] = {0.0, 0.002, 0.02, 0.1};
+  cudaEvent_t e0, e1;
+  PPR_CUDA_TRY(cudaEventCreate(&e0));
+  PPR_CUDA_TRY(cudaEventCreate(&e1));
+  double best_t = INFINITY;
+  ppr_query_opts best_o = o;
+  ppr_status s = PPR_OK;
+  for (int kt : kts) {
+    for (double f : fracs) {
+      ppr_query_opts c = o;
+      c.k_tile = kt;
+      c.switch_edges = (int64_t)(f * (double)g->m * kt);
+      // one untimed call allocates the workspace for this width
+      s = ppr_sssp_query(g, src, k, PPR_HP, &c, out_pi, nullptr, nullptr, nullptr, st);
+      if (s == PPR_ERR_ADMIT) { s = PPR_OK; break; }  // wider tiles do not fit: skip them
+      if (s != PPR_OK) break;
+      cudaEventRecord(e0, st);
+      s = ppr_sssp_query(g, src, k, PPR_HP, &c, out_pi, nullptr, nullptr, nullptr, st);
+      cudaEventRecord(e1, st);
+      if (s != PPR_OK) break;
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_t) {
+        best_t = ms;
+        best_o = c;
+      }
+    }
+    if (s != PPR_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != PPR_OK) return s;
+  *best = best_o;
+  if (best_ms) *best_ms = best_t;
+  const int b = tune_bucket(k);
+  g->tuned_kt[b] = best_o.k_tile;
+  g->tuned_switch_frac[b] = (double)best_o.switch_edges / ((double)g->m * best_o.k_tile);
+  return PPR_OK;
+}

@@ -486,7 +486,9 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
   const double rmax = lambda / (double)m;
   const u64 rmax_raw = (u64)std::max(1.0, std::floor(rmax * kFixOne));
   const u64 lambda_raw = (u64)std::floor(lambda * kFixOne);
-  const int64_t switch_edges = o.switch_edges >= 0 ? o.switch_edges : (int64_t)(0.02 * (double)m * KT);
+  const double tuned_frac = g->tuned_switch_frac[tune_bucket(k)];
+  const int64_t switch_edges = o.switch_edges >= 0 ? o.switch_edges
+                                                   : (int64_t)((tuned_frac >= 0 ? tuned_frac : 0.02) * (double)m * KT);
   int bps = 0;
   PPR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, sweep_kernel<KT>, 256, 0));
   const int sweep_grid = sm_count() * std::max(bps, 1);
@@ -799,6 +801,7 @@ int64_t hp_state_bytes(const ppr_graph* g, int32_t k, int32_t kt) {
 ppr_status query_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query_opts& o, double* out_pi,
                     double* out_r, ppr_stats* stats, cudaStream_t st) {
   int kt = o.k_tile;
+  if (kt == 0 && g->tuned_kt[tune_bucket(k)] > 0) kt = g->tuned_kt[tune_bucket(k)];
   if (kt == 0) {
     // one pass per tile: a wider tile costs less per source than two narrow ones
     kt = 1;

@@ -86,6 +86,9 @@ struct ppr_graph {
   int32_t* d_piece_e0 = nullptr;
   int32_t* d_heavy_npieces = nullptr;
   uint32_t stamp_epoch = 0;
+  // autotuned settings per k bucket (ceil(log2 k), 0..6); 0 / negative = untuned
+  int tuned_kt[7] = {0, 0, 0, 0, 0, 0, 0};
+  double tuned_switch_frac[7] = {-1, -1, -1, -1, -1, -1, -1};
   // per tile width: the sweep work list (index = log2 of the tile width, widths 1..64)
   struct SweepPlan {
     int kt = 0;
@@ -110,6 +113,7 @@ ppr_status warm_start_tile(const void* model, ppr_graph* g, const int32_t* src_n
                            unsigned long long* z0, cudaStream_t st);
 int warm_correction_passes(const void* model);
 int64_t hp_state_bytes(const ppr_graph* g, int32_t k, int32_t kt);
+int tune_bucket(int32_t k);
 ppr_status warm_correct_tile(const void* model, ppr_graph* g, const int32_t* src_new, int ncols, int kt, double alpha,
                              const unsigned long long* x, const unsigned long long* mass, unsigned long long* z,
                              cudaStream_t st);

@@ -204,3 +204,17 @@ def test_algorithm3_epochs_from_zero_start(P, c0, c0_ref):
     for i, s in enumerate(src[:4]):
         assert np.abs(pi[i] - c0_ref[int(s)]).sum() <= 2 * LAM
     check_bound_and_mass(st)
+
+
+def test_autotune_picks_a_setting_that_stays_exact(P, c0, c0_ref):
+    rp, ci, src = c0
+    g = P.Graph(rp, ci)
+    kt, sw, ms = g.autotune(src, lam=LAM)
+    assert kt in (1, 2, 4, 8, 16) and sw >= 0 and ms > 0
+    pi, st = g.query(src, P.PPR_HP, lam=LAM)  # k_tile = 0 and switch_edges = -1 now use the tuned values
+    torch.cuda.synchronize()
+    pi = pi.cpu().numpy()
+    for i, s in enumerate(src):
+        assert np.abs(pi[i] - c0_ref[int(s)]).sum() <= 2 * LAM
+    check_bound_and_mass(st)
+    g.close()
