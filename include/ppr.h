@@ -42,7 +42,10 @@ typedef enum {
   PPR_ERR_ADMIT = -6          /* not enough free device memory for the batch state */
 } ppr_status;
 
-#define PPR_FLAG_PARTIAL 1
+#define PPR_FLAG_PARTIAL 1 /* HP: stop after max_sweeps passes, uncertified */
+#define PPR_FLAG_SYNC 2    /* HP: every pass synchronous (SimFwdPush, equal to PowItr by Lemma 1);
+                              by default passes run in place except the certifying last
+                              pass of each batch (asynchronous updates, Sec. 5) */
 
 typedef enum {
   PPR_HP = 0,     /* high precision: ||pi_hat - pi||_1 <= lambda (PowerPush, Algorithm 3) */

@@ -18,6 +18,7 @@ PPR_OK, PPR_ERR_ARG, PPR_ERR_GRAPH, PPR_ERR_OOM = 0, -1, -2, -3
 PPR_ERR_NOT_CONVERGED, PPR_ERR_CUDA, PPR_ERR_ADMIT = -4, -5, -6
 PPR_HP, PPR_APPROX = 0, 1
 PPR_FLAG_PARTIAL = 1
+PPR_FLAG_SYNC = 2
 
 STATUS_NAMES = {0: "PPR_OK", -1: "PPR_ERR_ARG", -2: "PPR_ERR_GRAPH", -3: "PPR_ERR_OOM",
                 -4: "PPR_ERR_NOT_CONVERGED", -5: "PPR_ERR_CUDA", -6: "PPR_ERR_ADMIT"}

@@ -645,7 +645,16 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
       for (int c = 0; c < ncols; ++c) R = std::max(R, r0[c]);
       double rate = -1.0, prev_d = -1.0;  // observed contraction per pass
       int prev_sweeps = 0;
-      bool probe_next = warm;             // warm start: learn the rate before a long batch
+      // Passes run in place (one z buffer) except the last of each batch: rows
+      // then gather neighbours already updated in the same pass, the GPU form
+      // of the asynchronous pushes of Sec. 5 (chaotic relaxation of the same
+      // contraction, converging faster than synchronous passes).  The last
+      // pass of a batch is synchronous, so its measured ||x' - x||_1 / alpha is
+      // the exact residual norm of the estimate and certifies the stop.
+      // PPR_FLAG_SYNC keeps every pass synchronous (SimFwdPush = PowItr).
+      const bool sync_only = (o.flags & PPR_FLAG_SYNC) != 0;
+      bool probe_next = warm || !sync_only;  // learn the contraction rate before a long batch
+      int probe_len = warm ? 4 : 16;
       while (true) {
         // unknown residual (warm start): one pass measures it.  The residual
         // contracts at least by (1-alpha) per pass; once two measurements exist
@@ -655,7 +664,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
         int S = (!std::isfinite(R) || R <= lambda) ? 1
                                                     : (int)std::ceil(std::log(lambda / R) / std::log(cr) - 1e-12);
         S = std::max(S, 1);
-        if (rate <= 0.0 && probe_next) S = std::min(S, 4);
+        if (rate <= 0.0 && probe_next) S = std::min(S, probe_len);
         if (corr > 0 && !corrected) S = std::max(corr - sweeps, 1);  // passes before the correction
         if (partial) S = std::max(max_sweeps - sweeps, 0);
         if (partial && S == 0) break;
@@ -666,15 +675,16 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
         }
         PPR_CUDA_TRY(cudaEventRecord(es0, st));
         for (int j = 0; j < S; ++j) {
+          const bool sync_pass = sync_only || j == S - 1;
           sa.z_in = zcur;
-          sa.z_out = znext;
+          sa.z_out = sync_pass ? znext : zcur;
           sa.x_out = (j == S - 1) ? r : nullptr;
           // after two passes rows without in-edges hold their constant value in
           // both buffers; the pass that writes x still covers every row
           sa.n_items = (sweeps + j >= 2 && !sa.x_out) ? plan.n_items_nz : plan.n_items_all;
           sa.resid = resid + (size_t)(sweeps + j) * 64;
           launch_sweep<KT>(sa, sweep_grid, st);
-          std::swap(zcur, znext);
+          if (sync_pass) std::swap(zcur, znext);
         }
         PPR_CUDA_TRY(cudaEventRecord(es1, st));
         PPR_CUDA_TRY(cudaGetLastError());
@@ -722,6 +732,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
           rate = -1.0;        // the correction changes the residual: measure afresh
           prev_d = -1.0;
           probe_next = true;  // short first batch to learn the new contraction rate
+          probe_len = 4;
           continue;
         }
         if (ok) break;

@@ -67,11 +67,12 @@ def test_c0_chung_lu_against_powerpush(P, c0, c0_ref, k_tile):
 
 
 def test_lemma1_sweeps_equal_powitr(P, c0):
-    """With no queue phase every pass is one SimFwdPush iteration: 83 passes
-    for lambda = 1e-8, alpha = 0.2, equal to PowItr up to summation order."""
+    """With no queue phase and synchronous passes every pass is one SimFwdPush
+    iteration: 83 passes for lambda = 1e-8, alpha = 0.2, equal to PowItr up to
+    summation order."""
     rp, ci, src = c0
     og = O.Graph(rp, ci)
-    pi, st = run(P, rp, ci, src[:3], k_tile=4, switch_edges=0)
+    pi, st = run(P, rp, ci, src[:3], k_tile=4, switch_edges=0, flags=2)  # PPR_FLAG_SYNC
     for i, s in enumerate(src[:3]):
         ref, _, ost = O.powitr(og, int(s), ALPHA, LAM)
         assert ost["iterations"] == 83 and st[i]["sweeps"] == 83
@@ -218,3 +219,15 @@ def test_autotune_picks_a_setting_that_stays_exact(P, c0, c0_ref):
         assert np.abs(pi[i] - c0_ref[int(s)]).sum() <= 2 * LAM
     check_bound_and_mass(st)
     g.close()
+
+
+def test_asynchronous_passes_need_fewer_than_powitr(P, c0, c0_ref):
+    """Default in-place passes (asynchronous updates) certify the same bound
+    with fewer passes than the synchronous ones."""
+    rp, ci, src = c0
+    pi, st = run(P, rp, ci, src, switch_edges=0)
+    pi_s, st_s = run(P, rp, ci, src, switch_edges=0, flags=2)
+    for i, s in enumerate(src):
+        assert np.abs(pi[i] - c0_ref[int(s)]).sum() <= 2 * LAM
+    check_bound_and_mass(st)
+    assert st[0]["sweeps"] < st_s[0]["sweeps"] == 83
