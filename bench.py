@@ -135,12 +135,29 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_seed(base: int, rank: int) -> int:
+    """Each replica answers its own sources: the source seed is offset by rank
+    (queries are independent, so ranks exchange no data)."""
+    return base + 1000 * rank
+
+
+def max_over_ranks(value: float, device) -> float:
+    """The job's time is the slowest rank's (max all-reduce of one scalar)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_inputs(workload: str, rank: int):
     import ppr_inputs as gen
     scale, ef, k, kt = WORKLOADS[workload]
     rp, ci = gen.rmat(scale, ef, seed=1)
     seed = 3 if workload.endswith("approx") else 2
-    src = gen.sources(len(rp) - 1, k, seed=seed + 1000 * rank)
+    src = gen.sources(len(rp) - 1, k, seed=replica_seed(seed, rank))
     return rp, ci, src, kt
 
 
@@ -227,11 +244,7 @@ def run_gpu(args):
             sweeps.append(st[0]["sweeps"])
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), "cuda")
 
     # end to end: host source ids in, host (pinned) PPR vectors out, copies inside the timed region
     host_out = torch.empty((k, n), dtype=torch.float64, pin_memory=True)
@@ -246,10 +259,7 @@ def run_gpu(args):
         t = time.perf_counter()
         step(host_out)
         e2e_total += time.perf_counter() - t
-    if ws > 1:
-        t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(e2e_total, "cuda")
 
     # learned warm start (model trained on the workload's graph, held-out sources)
     warm = None
@@ -335,7 +345,7 @@ def warm_start_comparison(P, g, n, k, kt, out, flush, rank, train_n=4096, held_n
     import torch
     import ppr_inputs as gen
     train = gen.sources(n, train_n, seed=4)
-    held = gen.sources(n, held_n, seed=5 + 1000 * rank)
+    held = gen.sources(n, held_n, seed=replica_seed(5, rank))
     model = P.Model(g, seed=0x5EED, correction_passes=passes)
     t = time.perf_counter()
     losses = model.train(train, epochs=epochs, lr=2e-3, shuffle_seed=1)

@@ -1,0 +1,44 @@
+"""Multi-GPU runs are replicas (queries are independent): each rank answers
+its own sources and the job time is the slowest rank's.  The rank logic of
+bench.py is exercised here with two gloo processes on the CPU."""
+import os
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _worker(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    import ppr_inputs as gen
+    src = gen.sources(1 << 16, 64, seed=bench.replica_seed(2, rank))
+    slowest = bench.max_over_ranks(10.0 + rank, "cpu")
+    q.put((rank, src.tolist(), slowest))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_replicas_shard_sources_and_take_max_time():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 29500 + os.getpid() % 1000
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = {}
+    for _ in range(2):
+        rank, src, slowest = q.get(timeout=120)
+        res[rank] = (src, slowest)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res[0][0] != res[1][0]                  # different sources per replica
+    assert res[0][1] == res[1][1] == 11.0          # both ranks report the slowest time
