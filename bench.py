@@ -37,7 +37,9 @@ WORKLOADS = {
     "rmat20-k8": (20, 16, 8, 8),
     "rmat22-k1": (22, 16, 1, 1),
     "rmat22-approx": (22, 16, 16, 16),  # SpeedPPR, eps = 0.5, sources seed 3
+    "rmat22-index": (22, 16, 16, 16),   # SpeedPPR-Index (walks read from the index), same sources
 }
+APPROX_WORKLOADS = ("rmat22-approx", "rmat22-index")
 ALPHA, LAMBDA, EPS = 0.2, 1e-8, 0.5
 METRIC = "SSPPR queries/s at l1<=1e-8 (HP, plain GPU method)"
 METRIC_APPROX = "SSPPR queries/s, eps=0.5 relative error for pi>=1/n (SpeedPPR)"
@@ -156,7 +158,7 @@ def make_inputs(workload: str, rank: int):
     import ppr_inputs as gen
     scale, ef, k, kt = WORKLOADS[workload]
     rp, ci = gen.rmat(scale, ef, seed=1)
-    seed = 3 if workload.endswith("approx") else 2
+    seed = 3 if workload in APPROX_WORKLOADS else 2
     src = gen.sources(len(rp) - 1, k, seed=replica_seed(seed, rank))
     return rp, ci, src, kt
 
@@ -213,10 +215,15 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     out = torch.empty((k, n), dtype=torch.float64, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
-    approx = args.workload.endswith("approx")
+    approx = args.workload in APPROX_WORKLOADS
+    indexed = args.workload == "rmat22-index"
     opts = dict(lam=LAMBDA, alpha=ALPHA, k_tile=kt)
     if approx:
         opts = dict(eps=EPS, alpha=ALPHA, k_tile=kt)
+    if indexed:
+        # the index is built once per graph (preprocessing, outside the timed region)
+        g.build_index(0x1DE5, ALPHA)
+        opts["flags"] = P.PPR_FLAG_INDEX
     mode = P.PPR_APPROX if approx else P.PPR_HP
 
     def step(out_buf):
@@ -278,7 +285,14 @@ def run_gpu(args):
         return
 
     value = ws * k * args.steps / (total_ms / 1e3)
-    if approx:
+    if indexed:
+        # dominant kernel: the index reads; per walk one 4 B index entry and the
+        # two 32 B sectors of its endpoint's count and estimate
+        walks_total = sum(x["walks"] for x in st) * args.steps
+        per_launch = 68 * walks_total / args.steps
+        avg_sweep_ms = sweep_ms / args.steps
+        kernel_name = f"index_query_kernel<{kt}>"
+    elif approx:
         # dominant kernel: the walks; algorithmic bytes = two 32 B sectors per move
         steps_total = sum(x["walk_steps"] for x in st) * args.steps
         walks_total = sum(x["walks"] for x in st) * args.steps
@@ -305,6 +319,8 @@ def run_gpu(args):
             done += 1
         dt = time.perf_counter() - t
         alg = "Algorithm 4" if approx else "Algorithm 3"
+        if indexed:
+            alg = "Algorithm 4 with walks drawn per query (no index)"
         cpu = {"value": done / dt, "unit": "queries/s", "cores": 1, "kind": "oracle",
                "sample": f"{done} of the workload's sources, {alg} in FP64 on one host core"}
     rec = {

@@ -43,6 +43,7 @@ typedef enum {
 } ppr_status;
 
 #define PPR_FLAG_PARTIAL 1 /* HP: stop after max_sweeps passes, uncertified */
+#define PPR_FLAG_INDEX 4   /* APPROX: read the walks from the index of ppr_index_build */
 #define PPR_FLAG_SYNC 2    /* HP: every pass synchronous (SimFwdPush, equal to PowItr by Lemma 1);
                               by default passes run in place except the certifying last
                               pass of each batch (asynchronous updates, Sec. 5) */
@@ -174,6 +175,21 @@ int64_t ppr_query_state_bytes(const ppr_graph* g, int32_t k, int32_t k_tile);
  */
 ppr_status ppr_autotune(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query_opts* base, double* out_pi,
                         ppr_query_opts* best, double* best_ms, void* cuda_stream);
+
+/*
+ * SpeedPPR-Index (Sec. 6.2): SpeedPPR needs at most d_v walks from a node v,
+ * so the endpoints of d_v alpha-walks per node (m int32 in all, independent
+ * of eps) answer every approximate query.  The walk stored for the caller's
+ * out-edge slot e (row_ptr[v] + k) uses Philox-4x32-10 with key (seed_lo,
+ * seed_hi) and counter (e_lo, e_hi, t/2, 0x1D3A), words as in the walk phase.
+ * ppr_sssp_query(..., PPR_APPROX) with flags PPR_FLAG_INDEX then reads, for
+ * each v with r(v) > 0, the first W_v = min(ceil(r(v) W), d_v) stored
+ * endpoints of v instead of walking.  Builds on the device (4 m bytes, kept
+ * with the graph).  ppr_index_get copies the endpoints to a host int32[m] in
+ * the caller's slot order and node ids.
+ */
+ppr_status ppr_index_build(ppr_graph* g, uint64_t seed, double alpha, void* cuda_stream);
+ppr_status ppr_index_get(const ppr_graph* g, int32_t* endpoints);
 
 /* Release the graph and every device buffer it owns; NULL is allowed. */
 void ppr_free(ppr_graph* g);

@@ -83,6 +83,10 @@ def _load():
                 f.restype = ctypes.c_int
             lib.orc_philox4x32_10.argtypes = [P, P, P]
             lib.orc_philox4x32_10.restype = None
+            lib.orc_build_walk_index.argtypes = [I64, P, P, D, U64, I64, P]
+            lib.orc_build_walk_index.restype = ctypes.c_int
+            lib.orc_index_walks.argtypes = [I64, P, P, P, D, P, P, S]
+            lib.orc_index_walks.restype = ctypes.c_int
             lib.orc_gaussian_rows.argtypes = [I64, I64, ctypes.c_int, U64, P]
             lib.orc_gaussian_rows.restype = None
             lib.orc_speedppr_W.argtypes = [I64, D, D]
@@ -236,3 +240,22 @@ def gaussian_rows(u0: int, count: int, F: int, seed: int) -> np.ndarray:
     out = np.zeros((count, F))
     _load().orc_gaussian_rows(u0, count, F, seed, out.ctypes.data)
     return out
+
+
+def build_walk_index(g: Graph, seed: int, alpha: float = 0.2, max_steps: int = 1 << 16) -> np.ndarray:
+    """SpeedPPR-Index: endpoint of the walk stored for every edge slot (m entries)."""
+    idx = np.zeros(max(g.m, 1), dtype=np.int32)
+    _rc(_load().orc_build_walk_index(*g.args(), alpha, seed, max_steps, idx.ctypes.data), "build_walk_index")
+    return idx[:g.m]
+
+
+def index_walks(g: Graph, index: np.ndarray, r: np.ndarray, W: float):
+    """Walk phase of Algorithm 4 read from the index; returns (counts, est, stats)."""
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    idx = np.ascontiguousarray(index, dtype=np.int32)
+    counts = np.zeros(g.n, dtype=np.uint32)
+    est = np.zeros(g.n)
+    st = Stats()
+    _rc(_load().orc_index_walks(g.n, g.row_ptr.ctypes.data, idx.ctypes.data, r.ctypes.data, W, counts.ctypes.data,
+                                est.ctypes.data, ctypes.byref(st)), "index_walks")
+    return counts, est, st.as_dict()

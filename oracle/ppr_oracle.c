@@ -27,6 +27,8 @@
  *   orc_philox4x32_10   Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
  *   orc_gaussian_rows   rows of the fixed random feature matrix of the learned
  *                       warm start (Box-Muller on Philox words)
+ *   orc_build_walk_index, orc_index_walks
+ *                       SpeedPPR-Index: d_v stored walks per node (Sec. 6.2)
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -535,4 +537,67 @@ void orc_gaussian_rows(int64_t u0, int64_t count, int F, uint64_t seed, double* 
       }
     }
   }
+}
+
+/* ------------------------------------------------------------ SpeedPPR-Index */
+/*
+ * The index of Sec. 6.2 ("Improvements over FORA"): SpeedPPR needs at most
+ * d_v walks from each node v, so d_v walks per node, m in total, answer every
+ * eps.  Walk k of node v belongs to edge slot e = row_ptr[v] + k: it is the
+ * alpha-walk of orc_walks with Philox counter (e_lo, e_hi, t/2, 0x1D3A) under
+ * key (seed_lo, seed_hi).  index[e] receives its endpoint.
+ */
+int orc_build_walk_index(int64_t n, const int64_t* rp, const int32_t* ci, double alpha, uint64_t seed,
+                         int64_t max_steps, int32_t* index) {
+  if (n < 1 || !rp || !ci || !index || !(alpha > 0 && alpha < 1)) return ORC_ERR_ARG;
+  const uint32_t stop_below = (uint32_t)floor(alpha * 4294967296.0);
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int64_t v = 0; v < n; ++v) {
+    for (int64_t e = rp[v]; e < rp[v + 1]; ++e) {
+      int64_t cur = v;
+      uint32_t words[4];
+      for (int64_t t = 0;; ++t) {
+        if ((t & 1) == 0) {
+          uint32_t ctr[4] = {(uint32_t)e, (uint32_t)((uint64_t)e >> 32), (uint32_t)(t >> 1), 0x1D3Au};
+          orc_philox4x32_10(ctr, key, words);
+        }
+        if (words[2 * (t & 1)] < stop_below) break;
+        if (t >= max_steps) return ORC_ERR_NOT_CONVERGED;
+        int64_t d = rp[cur + 1] - rp[cur];
+        cur = ci[rp[cur] + (int64_t)(((uint64_t)words[2 * (t & 1) + 1] * (uint64_t)d) >> 32)];
+      }
+      index[e] = (int32_t)cur;
+    }
+  }
+  return ORC_OK;
+}
+
+/*
+ * Algorithm 4's walk phase read from the index: for each v with r(v) > 0,
+ * W_v = ceil(r(v) W) (at most d_v after the refinement; capped at d_v so that
+ * float rounding of the residue cannot ask for more walks than stored), and
+ * the endpoints of v's first W_v index walks each add r(v)/W_v to est and 1
+ * to counts.
+ */
+int orc_index_walks(int64_t n, const int64_t* rp, const int32_t* index, const double* r, double W,
+                    uint32_t* counts, double* est, orc_stats* st) {
+  if (n < 1 || !rp || !index || !r || !counts || !est || !(W > 0)) return ORC_ERR_ARG;
+  memset(counts, 0, sizeof(uint32_t) * (size_t)n);
+  memset(est, 0, sizeof(double) * (size_t)n);
+  int64_t walks = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    if (!(r[v] > 0.0)) continue;
+    int64_t d = rp[v + 1] - rp[v];
+    int64_t Wv = (int64_t)ceil(r[v] * W);
+    if (Wv > d) Wv = d;
+    double inc = r[v] / (double)Wv;
+    for (int64_t k = 0; k < Wv; ++k) {
+      int32_t u = index[rp[v] + k];
+      counts[u] += 1;
+      est[u] += inc;
+    }
+    walks += Wv;
+  }
+  if (st) { memset(st, 0, sizeof(*st)); st->walks = walks; st->W = W; }
+  return ORC_OK;
 }

@@ -19,6 +19,7 @@ PPR_ERR_NOT_CONVERGED, PPR_ERR_CUDA, PPR_ERR_ADMIT = -4, -5, -6
 PPR_HP, PPR_APPROX = 0, 1
 PPR_FLAG_PARTIAL = 1
 PPR_FLAG_SYNC = 2
+PPR_FLAG_INDEX = 4
 
 STATUS_NAMES = {0: "PPR_OK", -1: "PPR_ERR_ARG", -2: "PPR_ERR_GRAPH", -3: "PPR_ERR_OOM",
                 -4: "PPR_ERR_NOT_CONVERGED", -5: "PPR_ERR_CUDA", -6: "PPR_ERR_ADMIT"}
@@ -98,6 +99,8 @@ SIGNATURES = {
     "ppr_graph_n": (ctypes.c_int64, [_P]),
     "ppr_graph_m": (ctypes.c_int64, [_P]),
     "ppr_query_state_bytes": (ctypes.c_int64, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "ppr_index_build": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double, _P]),
+    "ppr_index_get": (ctypes.c_int, [_P, _P]),
     "ppr_autotune": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(ppr_query_opts), _P,
                                     ctypes.POINTER(ppr_query_opts), ctypes.POINTER(ctypes.c_double), _P]),
     "ppr_model_default_opts": (None, [ctypes.POINTER(ppr_model_opts)]),
@@ -242,6 +245,15 @@ class Graph:
         _check(load_library().ppr_autotune(self.handle, s.ctypes.data, len(s), ctypes.byref(base), _ptr(out),
                                            ctypes.byref(best), ctypes.byref(ms), _stream(stream)))
         return best.k_tile, best.switch_edges, ms.value
+
+    def build_index(self, seed: int = 0x5EED, alpha: float = 0.2, stream=None):
+        """SpeedPPR-Index: d_v stored walks per node (m endpoints) on the device."""
+        _check(load_library().ppr_index_build(self.handle, seed, alpha, _stream(stream)))
+
+    def get_index(self) -> np.ndarray:
+        out = np.zeros(max(self.m, 1), dtype=np.int32)
+        _check(load_library().ppr_index_get(self.handle, out.ctypes.data))
+        return out[:self.m]
 
     def state_bytes(self, k: int, k_tile: int = 0) -> int:
         """Device workspace of a high-precision query of k sources."""

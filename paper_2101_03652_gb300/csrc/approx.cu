@@ -449,6 +449,14 @@ __global__ void apx_finish_kernel(int64_t n, const int32_t* __restrict__ new_of_
 }
 
 // ------------------------------------------------------------ host engine
+// a node with more than 32 index walks in a column goes to a block; at most
+// m / 32 such nodes per column
+inline size_t index_heavy_bytes(int64_t m, int kt) { return ((size_t)m * kt / 32 + 1024 + 8) * sizeof(u64); }
+
+template <int KT>
+ppr_status index_walk_phase(ppr_graph* g, const float* r, double W, int ncols, unsigned* counts, double* est,
+                            u64* walks, cudaStream_t st);
+
 template <int KT>
 static ppr_status run_approx(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query_opts& o, double* out_pi,
                              double* out_r, uint32_t* out_counts, ppr_stats* stats, cudaStream_t st) {
@@ -474,7 +482,8 @@ static ppr_status run_approx(ppr_graph* g, const int32_t* src, int32_t k, const 
   if (pi_host) stage += (size_t)k * n * 8;
   if (r_host) stage += (size_t)k * n * 8;
   if (c_host) stage += (size_t)k * n * 4;
-  const size_t need = cells * 4 * 4 + cells * 8 + cells * 4 + (size_t)KT * (n + 1) * 8 + (size_t)KT * nscan * 8 +
+  const size_t walk_b_bytes = (o.flags & PPR_FLAG_INDEX) ? index_heavy_bytes(m, KT) : (size_t)KT * (n + 1) * 8;
+  const size_t need = cells * 4 * 4 + cells * 8 + cells * 4 + walk_b_bytes + (size_t)KT * nscan * 8 +
                       (size_t)plan->n_split * KT * 4 + stage;
   {
     size_t free_b = 0, total_b = 0;
@@ -486,7 +495,13 @@ static ppr_status run_approx(ppr_graph* g, const int32_t* src, int32_t k, const 
     }
   }
   PPR_TRY(ws.walk_a.ensure(cells * 4 * 4 + cells * 8 + cells * 4));  // r, pi, ya, yb | est | counts
-  PPR_TRY(ws.walk_b.ensure((size_t)KT * (n + 1) * 8));               // walk offsets
+  const bool use_index = (o.flags & PPR_FLAG_INDEX) != 0;
+  if (use_index && (!g->d_index || g->index_alpha != alpha)) {
+    set_error(g->d_index ? "the walk index was built for another alpha" : "PPR_FLAG_INDEX needs ppr_index_build first");
+    return PPR_ERR_ARG;
+  }
+  // walk offsets, or the heavy (node, column) list of an index query
+  PPR_TRY(ws.walk_b.ensure(walk_b_bytes));
   PPR_TRY(ws.walk_c.ensure((size_t)KT * nscan * 8 + 4096));          // scan sums, counters
   const size_t acc_bytes = std::max<size_t>((size_t)plan->n_split * KT * 4, 4);
   const size_t cnt_bytes = std::max<size_t>((size_t)plan->n_split * 4, 4);
@@ -590,8 +605,31 @@ static ppr_status run_approx(ppr_graph* g, const int32_t* src, int32_t k, const 
     }
     if (status_out != PPR_OK) break;
     PPR_CUDA_TRY(cudaEventRecord(e1, st));
-    // ---- walks
-    {
+    // ---- walks (from the index when one is built and requested)
+    if (use_index) {
+      PPR_TRY(index_walk_phase<KT>(g, r, W, ncols, counts, est, ctr, st));
+      PPR_CUDA_TRY(cudaEventRecord(e2, st));
+      apx_finish_kernel<KT><<<grid_ew, 256, 0, st>>>(n, g->d_new_of_old, pi, est, r, counts, ncols, t0, pi_dev, r_dev,
+                                                     c_dev);
+      launches += 3;
+      PPR_CUDA_TRY(cudaGetLastError());
+      PPR_CUDA_TRY(cudaMemcpyAsync(hpin, ctr, 8 * KT, cudaMemcpyDeviceToHost, st));
+      PPR_CUDA_TRY(cudaStreamSynchronize(st));
+      float a1 = 0.f, a2 = 0.f;
+      cudaEventElapsedTime(&a1, e0, e1);
+      cudaEventElapsedTime(&a2, e1, e2);
+      ms_push += a1;
+      ms_walk += a2;
+      if (stats)
+        for (int c = 0; c < ncols; ++c) {
+          ppr_stats& sx = stats[t0 + c];
+          memset(&sx, 0, sizeof(sx));
+          sx.sweeps = sweeps;
+          sx.edges_swept = (int64_t)sweeps * m;
+          sx.walks = (int64_t)hpin[c];
+          sx.W = W;
+        }
+    } else {
       dim3 gc(grid_ew, ncols);
       walk_count_kernel<KT><<<gc, 256, 0, st>>>(n, g->d_new_of_old, r, W, ncols, offs);
       dim3 gs((unsigned)nscan, ncols);
@@ -707,3 +745,197 @@ ppr_status query_approx(ppr_graph* g, const int32_t* src, int32_t k, const ppr_q
 }
 
 }  // namespace ppr
+
+// ========================================================= SpeedPPR-Index
+// SpeedPPR needs at most d_v walks from a node v (Sec. 6.2), so the endpoints
+// of d_v walks per node -- m in all -- answer every eps.  The walk stored for
+// out-edge slot e (the caller's CSR position of v's k-th out-edge) uses
+// Philox-4x32-10 with counter (e_lo, e_hi, t/2, 0x1D3A); the endpoint is kept
+// at the slot of the relabelled out-CSR that holds the same edge.
+namespace ppr {
+
+constexpr int kIndexSlotsPerThread = 16;
+
+__global__ void __launch_bounds__(256) index_build_kernel(int64_t n, int64_t m, const int32_t* __restrict__ out_rp,
+                                                          const int32_t* __restrict__ out_ci,
+                                                          const int32_t* __restrict__ old_of_new,
+                                                          const int64_t* __restrict__ rp_orig, uint32_t key0,
+                                                          uint32_t key1, uint32_t stop_below, int32_t max_steps,
+                                                          int32_t* __restrict__ index, int* status) {
+  const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kIndexSlotsPerThread;
+  if (j0 >= m) return;
+  const int64_t j1 = min(j0 + (int64_t)kIndexSlotsPerThread, m);
+  int64_t lo = 0, hi = n - 1;  // node owning slot j0: last u with out_rp[u] <= j0
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (out_rp[mid] <= j0) lo = mid; else hi = mid - 1;
+  }
+  int64_t u = lo;
+  for (int64_t j = j0; j < j1; ++j) {
+    while (out_rp[u + 1] <= j) ++u;
+    const int64_t e = rp_orig[old_of_new[u]] + (j - out_rp[u]);
+    int32_t cur = (int32_t)u;
+    uint4 words = make_uint4(0, 0, 0, 0);
+    bool ok = true;
+    for (int32_t t = 0;; ++t) {
+      if ((t & 1) == 0)
+        words = philox4x32_10(make_uint4((uint32_t)e, (uint32_t)((u64)e >> 32), (uint32_t)(t >> 1), 0x1D3Au), key0,
+                              key1);
+      if (((t & 1) ? words.z : words.x) < stop_below) break;
+      if (t >= max_steps) { ok = false; break; }
+      const int32_t e0 = __ldg(&out_rp[cur]);
+      const int32_t d = __ldg(&out_rp[cur + 1]) - e0;
+      cur = __ldg(&out_ci[e0 + (int32_t)__umulhi((t & 1) ? words.w : words.y, (uint32_t)d)]);
+    }
+    if (!ok) atomicExch(status, 1);
+    index[j] = cur;
+  }
+}
+
+// walk phase from the index: W_v = min(ceil(r(v) W), d_v) stored endpoints of v
+template <int KT>
+__global__ void __launch_bounds__(256) index_query_kernel(int64_t n, const int32_t* __restrict__ out_rp,
+                                                          const int32_t* __restrict__ index,
+                                                          const float* __restrict__ r, double W,
+                                                          unsigned* __restrict__ counts, double* __restrict__ est,
+                                                          u64* __restrict__ heavy, u64* __restrict__ n_heavy,
+                                                          u64* __restrict__ walks) {
+  const int c = blockIdx.y;
+  u64 mine = 0;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    const float rv = r[(size_t)u * KT + c];
+    if (!(rv > 0.f)) continue;
+    const int32_t e0 = out_rp[u];
+    const int64_t d = out_rp[u + 1] - e0;
+    const int64_t wv = min((int64_t)ceil(__dmul_rn((double)rv, W)), d);
+    mine += (u64)wv;
+    if (wv > 32) {
+      heavy[atomicAdd(n_heavy, 1ull)] = ((u64)u << 6) | (u64)c;
+      continue;
+    }
+    const double inc = (double)rv / (double)wv;
+    for (int64_t k = 0; k < wv; ++k) {
+      const int32_t t = __ldg(&index[e0 + k]);
+      atomicAdd(&counts[(size_t)t * KT + c], 1u);
+      atomicAdd(&est[(size_t)t * KT + c], inc);
+    }
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) mine += __shfl_xor_sync(kAllLanes, mine, off);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&walks[c], mine);
+}
+
+template <int KT>
+__global__ void __launch_bounds__(256) index_query_heavy_kernel(const int32_t* __restrict__ out_rp,
+                                                                const int32_t* __restrict__ index,
+                                                                const float* __restrict__ r, double W,
+                                                                const u64* __restrict__ heavy,
+                                                                const u64* __restrict__ n_heavy,
+                                                                unsigned* __restrict__ counts,
+                                                                double* __restrict__ est) {
+  const u64 nh = *n_heavy;
+  for (u64 h = blockIdx.x; h < nh; h += gridDim.x) {
+    const u64 rec = heavy[h];
+    const int64_t u = (int64_t)(rec >> 6);
+    const int c = (int)(rec & 63);
+    const float rv = r[(size_t)u * KT + c];
+    const int32_t e0 = out_rp[u];
+    const int64_t d = out_rp[u + 1] - e0;
+    const int64_t wv = min((int64_t)ceil(__dmul_rn((double)rv, W)), d);
+    const double inc = (double)rv / (double)wv;
+    for (int64_t k = threadIdx.x; k < wv; k += blockDim.x) {
+      const int32_t t = __ldg(&index[e0 + k]);
+      atomicAdd(&counts[(size_t)t * KT + c], 1u);
+      atomicAdd(&est[(size_t)t * KT + c], inc);
+    }
+  }
+}
+
+template <int KT>
+ppr_status index_walk_phase(ppr_graph* g, const float* r, double W, int ncols, unsigned* counts, double* est,
+                            u64* walks, cudaStream_t st) {
+  const int64_t n = g->n;
+  if (g->ws.walk_b.bytes < index_heavy_bytes(g->m, KT)) {
+    set_error("index query workspace too small");
+    return PPR_ERR_ARG;
+  }
+  u64* nh = g->ws.walk_b.as<u64>();
+  u64* heavy = nh + 8;
+  PPR_CUDA_TRY(cudaMemsetAsync(nh, 0, sizeof(u64), st));
+  PPR_CUDA_TRY(cudaMemsetAsync(walks, 0, sizeof(u64) * KT, st));
+  const int grid = sm_count() * 8;
+  index_query_kernel<KT><<<dim3(grid, ncols), 256, 0, st>>>(n, g->d_out_rp, g->d_index, r, W, counts, est, heavy, nh,
+                                                            walks);
+  index_query_heavy_kernel<KT><<<grid, 256, 0, st>>>(g->d_out_rp, g->d_index, r, W, heavy, nh, counts, est);
+  PPR_CUDA_TRY(cudaGetLastError());
+  return PPR_OK;
+}
+
+}  // namespace ppr
+
+using namespace ppr;
+
+extern "C" ppr_status ppr_index_build(ppr_graph* g, uint64_t seed, double alpha, void* cuda_stream) {
+  clear_error();
+  if (!g || !(alpha > 0.0 && alpha < 1.0)) {
+    set_error("index_build needs a graph and alpha in (0, 1)");
+    return PPR_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int64_t n = g->n, m = g->m;
+  // the caller's row pointers (original order) from the stored out-degrees
+  std::vector<int64_t> rp(n + 1, 0);
+  for (int64_t v = 0; v < n; ++v) rp[v + 1] = rp[v] + g->h_out_deg[g->h_new_of_old[v]];
+  int64_t* d_rp = nullptr;
+  int* d_status = nullptr;
+  PPR_CUDA_TRY(cudaMalloc(&d_rp, sizeof(int64_t) * (n + 1)));
+  if (cudaMalloc(&d_status, sizeof(int)) != cudaSuccess) {
+    cudaFree(d_rp);
+    set_error("out of device memory");
+    return PPR_ERR_OOM;
+  }
+  if (!g->d_index && cudaMalloc(&g->d_index, sizeof(int32_t) * std::max<int64_t>(m, 1)) != cudaSuccess) {
+    g->d_index = nullptr;
+    cudaFree(d_rp);
+    cudaFree(d_status);
+    set_error("out of device memory for the walk index (%lld bytes)", (long long)(4 * m));
+    return PPR_ERR_OOM;
+  }
+  cudaMemcpyAsync(d_rp, rp.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(d_status, 0, sizeof(int), st);
+  const int64_t threads = (m + kIndexSlotsPerThread - 1) / kIndexSlotsPerThread;
+  index_build_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+      n, m, g->d_out_rp, g->d_out_ci, g->d_old_of_new, d_rp, (uint32_t)seed, (uint32_t)(seed >> 32),
+      (uint32_t)std::floor(alpha * 4294967296.0), 1 << 16, g->d_index, d_status);
+  int status = 0;
+  cudaError_t e = cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d_rp);
+  cudaFree(d_status);
+  PPR_CUDA_TRY(e);
+  if (status) {
+    set_error("an index walk exceeded 2^16 steps");
+    return PPR_ERR_NOT_CONVERGED;
+  }
+  g->index_seed = seed;
+  g->index_alpha = alpha;
+  return PPR_OK;
+}
+
+extern "C" ppr_status ppr_index_get(const ppr_graph* g, int32_t* endpoints) {
+  clear_error();
+  if (!g || !endpoints) { set_error("graph and endpoints must be non-NULL"); return PPR_ERR_ARG; }
+  if (!g->d_index) { set_error("no walk index built for this graph"); return PPR_ERR_ARG; }
+  const int64_t n = g->n, m = g->m;
+  std::vector<int32_t> idx(m), rp_new(n + 1, 0);
+  PPR_CUDA_TRY(cudaMemcpy(idx.data(), g->d_index, sizeof(int32_t) * m, cudaMemcpyDeviceToHost));
+  PPR_CUDA_TRY(cudaMemcpy(rp_new.data(), g->d_out_rp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost));
+  std::vector<int32_t> old_of_new(n);
+  for (int64_t v = 0; v < n; ++v) old_of_new[g->h_new_of_old[v]] = (int32_t)v;
+  int64_t e = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    const int64_t u = g->h_new_of_old[v];
+    for (int64_t j = rp_new[u]; j < rp_new[u + 1]; ++j) endpoints[e++] = old_of_new[idx[j]];
+  }
+  return PPR_OK;
+}

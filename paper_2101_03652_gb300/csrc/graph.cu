@@ -137,7 +137,7 @@ static ppr_status upload(T** dst, const T* src, size_t count, cudaStream_t st) {
 static void free_graph_arrays(ppr_graph* g) {
   for (void* p : {(void*)g->d_new_of_old, (void*)g->d_old_of_new, (void*)g->d_out_rp, (void*)g->d_out_ci,
                   (void*)g->d_in_rp, (void*)g->d_in_ci, (void*)g->d_deg, (void*)g->d_omega, (void*)g->d_invw,
-                  (void*)g->d_piece_row, (void*)g->d_piece_e0, (void*)g->d_heavy_npieces})
+                  (void*)g->d_piece_row, (void*)g->d_piece_e0, (void*)g->d_heavy_npieces, (void*)g->d_index})
     if (p) cudaFree(p);
   for (auto& pl : g->plans) {
     if (pl.d_items) cudaFree(pl.d_items);
@@ -168,6 +168,7 @@ static ppr_status build_and_upload(ppr_graph* g, const int64_t* rp, const int32_
     deg[i] = (int32_t)(rp[v + 1] - rp[v]);
     out_rp[i + 1] = out_rp[i] + deg[i];
   }
+  g->h_out_deg = deg;
   std::vector<int32_t> out_ci(m);
   {
     int threads = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));

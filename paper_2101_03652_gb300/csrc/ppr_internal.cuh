@@ -68,6 +68,7 @@ struct ppr_graph {
   // relabelling: nodes sorted by in-degree (descending, ties by original id)
   std::vector<int32_t> h_new_of_old;   // new id of an original id
   std::vector<int32_t> h_in_deg_sorted;  // in-degree of new id (non-increasing)
+  std::vector<int32_t> h_out_deg;        // out-degree of new id
   int32_t* d_new_of_old = nullptr;     // n
   int32_t* d_old_of_new = nullptr;     // n
   int32_t* d_out_rp = nullptr;         // n+1, out-CSR in new ids (original neighbour order)
@@ -86,6 +87,10 @@ struct ppr_graph {
   int32_t* d_piece_e0 = nullptr;
   int32_t* d_heavy_npieces = nullptr;
   uint32_t stamp_epoch = 0;
+  // SpeedPPR-Index: endpoint (new id) of the stored walk of every out-edge slot
+  int32_t* d_index = nullptr;
+  uint64_t index_seed = 0;
+  double index_alpha = 0.0;
   // autotuned settings per k bucket (ceil(log2 k), 0..6); 0 / negative = untuned
   int tuned_kt[7] = {0, 0, 0, 0, 0, 0, 0};
   double tuned_switch_frac[7] = {-1, -1, -1, -1, -1, -1, -1};

@@ -316,3 +316,39 @@ def test_W_equation8_values():
     n = 1 << 22
     W = O.speedppr_W(n, 0.5, 1.0 / n)
     assert abs(W - 1.19391e9) / 1.19391e9 < 1e-4
+
+
+def test_walk_index_endpoints_follow_ppr():
+    """Index walks are alpha-walks: the d_v stored endpoints of the nodes of a
+    small graph, pooled over many seeds, follow pi_v (chi-square)."""
+    g = O.Graph(*gen.fig1_graph())
+    v = 1  # d_v = 4
+    counts = np.zeros(g.n)
+    for seed in range(20000):
+        idx = O.build_walk_index(g, seed)
+        for e in range(g.row_ptr[v], g.row_ptr[v + 1]):
+            counts[idx[e]] += 1
+    total = counts.sum()
+    exact = lapack_ppr(g, v)
+    chi2 = ((counts - total * exact) ** 2 / (total * exact)).sum()
+    assert chi2 < 20.5
+
+
+def test_index_query_reads_first_walks():
+    """With W_v <= d_v the index query uses v's first W_v stored walks."""
+    g = O.Graph(*gen.chung_lu(500, 5000, 2.2, seed=2))
+    idx = O.build_walk_index(g, 9)
+    rng = np.random.default_rng(1)
+    d = np.diff(g.row_ptr)
+    W = 1000.0
+    r = rng.random(g.n) * d / W            # no node active w.r.t. 1/W
+    r[rng.random(g.n) < 0.3] = 0.0
+    counts, est, st = O.index_walks(g, idx, r, W)
+    expect = np.zeros(g.n)
+    for v in np.nonzero(r > 0)[0]:
+        Wv = int(np.ceil(r[v] * W))
+        assert Wv <= d[v]
+        for u in idx[g.row_ptr[v]:g.row_ptr[v] + Wv]:
+            expect[u] += 1
+    assert np.array_equal(counts, expect.astype(np.uint32))
+    assert abs(est.sum() - r.sum()) < 1e-12
