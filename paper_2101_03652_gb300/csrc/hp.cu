@@ -493,6 +493,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
   PPR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, sweep_kernel<KT>, 256, 0));
   const int sweep_grid = sm_count() * std::max(bps, 1);
 
+
   const int grid_ew = sm_count() * 8;
 
   cudaEvent_t ev0, ev1, ev2, es0, es1;
@@ -682,7 +683,8 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
           // after two passes rows without in-edges hold their constant value in
           // both buffers; the pass that writes x still covers every row
           sa.n_items = (sweeps + j >= 2 && !sa.x_out) ? plan.n_items_nz : plan.n_items_all;
-          sa.resid = resid + (size_t)(sweeps + j) * 64;
+          // only the last pass of a batch has its residual read back
+          sa.resid = j == S - 1 ? resid + (size_t)(sweeps + j) * 64 : nullptr;
           launch_sweep<KT>(sa, sweep_grid, st);
           if (sync_pass) std::swap(zcur, znext);
         }

@@ -32,7 +32,7 @@ struct SweepArgs {
   u64* x_out;        // optional: the estimate x of this pass
   int32_t src[64];   // tile's sources (new ids), -1 for unused columns
   u64 alpha_raw;     // alpha in Q1.63
-  double* resid;     // [KT] sums of |x_new - x_old| in raw units (this pass)
+  double* resid;     // [KT] sums of |x_new - x_old| in raw units (this pass); NULL: not needed
   const int32_t* heavy_npieces;
   u64* heavy_acc;
   unsigned int* heavy_cnt;
@@ -75,15 +75,18 @@ __device__ __forceinline__ void row_epilogue(const SweepArgs& a, int u, int slot
   constexpr int V = Lay<KT>::V;
   const u64 om = __ldg(&a.omega[u]);
   const float iw = __ldg(&a.invw[u]);
-  u64 zo[V], zn[V], xn[V];
-  ld_vec<V>(a.z_in + (size_t)u * KT + slot * V, zo);
+  u64 zn[V], xn[V];
 #pragma unroll
   for (int q = 0; q < V; ++q) {
     const int c = slot * V + q;
     xn[q] = acc[q] + (u == a.src[c] ? a.alpha_raw : 0ull);
     zn[q] = mulhi_round(xn[q], om);
-    const u64 dz = zn[q] > zo[q] ? zn[q] - zo[q] : zo[q] - zn[q];
-    res[q] += (float)dz * iw;
+  }
+  if (a.resid) {
+    u64 zo[V];
+    ld_vec<V>(a.z_in + (size_t)u * KT + slot * V, zo);
+#pragma unroll
+    for (int q = 0; q < V; ++q) res[q] += (float)(zn[q] > zo[q] ? zn[q] - zo[q] : zo[q] - zn[q]) * iw;
   }
   st_vec<V>(a.z_out + (size_t)u * KT + slot * V, zn);
   if (a.x_out) st_vec<V>(a.x_out + (size_t)u * KT + slot * V, xn);
@@ -193,6 +196,7 @@ __global__ void __launch_bounds__(256, 6) sweep_kernel(SweepArgs a) {
     }
   }
 
+  if (!a.resid) return;
   // per-column residual: lanes with equal slot, then warps, then one atomic per column
   __shared__ float sred[8][KT];
 #pragma unroll
