@@ -108,22 +108,36 @@ def sweep_bytes(n: int, m: int, kt: int) -> int:
     return 4 * (n + 1) + 4 * m + 12 * n + 16 * n * kt
 
 
-def kernel_source_sha() -> str:
+def fp32_pass_bytes(n: int, m: int, kt: int) -> int:
+    """Algorithmic bytes of one FP32 correction pass: in-CSR (4(n+1) + 4m),
+    degrees (4n), z_e gathered once and written once and r_f read once (12 n kt)."""
+    return 4 * (n + 1) + 4 * m + 4 * n + 12 * n * kt
+
+
+TRAFFIC_FILES = {
+    # kernel family: (committed ncu summary, sources the capture was taken on)
+    "sweep_kernel": ("sweep_kernel_traffic.json", ("sweep_kernel.cuh",)),
+    "refine_pass_kernel": ("refine_pass_kernel_traffic.json", ("refine_kernel.cuh", "f32_lanes.cuh", "sweep_kernel.cuh")),
+}
+
+
+def kernel_source_sha(sources=("sweep_kernel.cuh",)) -> str:
     h = hashlib.sha256()
-    for name in ("sweep_kernel.cuh",):
+    for name in sources:
         with open(os.path.join(ROOT, "paper_2101_03652_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload: str):
-    """DRAM bytes per sweep launch from the committed ncu summary, if it was
-    taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "sweep_kernel_traffic.json")
+def ncu_traffic(workload: str, kernel: str = "sweep_kernel"):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    fname, sources = TRAFFIC_FILES[kernel]
+    path = os.path.join(ROOT, "profiles", fname)
     try:
         with open(path) as f:
             rec = json.load(f)
-        if rec.get("kernel_source_sha") == kernel_source_sha() and workload in rec.get("workloads", []):
+        if rec.get("kernel_source_sha") == kernel_source_sha(sources) and workload in rec.get("workloads", []):
             return float(rec["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -236,6 +250,7 @@ def run_gpu(args):
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     sweep_ms, sweep_launches, launches, sweeps = 0.0, 0, 0, []
+    fp32_ms, fp32_launches = 0.0, 0
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -247,6 +262,9 @@ def run_gpu(args):
             ev[i][1].record(stream)
             sweep_ms += st[0]["ms_sweep"] if not approx else st[0]["ms_walk"]
             sweep_launches += st[0]["sweep_launches"]
+            if not approx:
+                fp32_ms += st[0]["ms_fp32"]
+                fp32_launches += sum(st[t]["fp32_passes"] for t in range(0, k, kt))
             launches += st[0]["kernel_launches"]
             sweeps.append(st[0]["sweeps"])
         torch.cuda.synchronize()
@@ -299,6 +317,11 @@ def run_gpu(args):
         per_launch = 64 * (steps_total + walks_total) / args.steps
         avg_sweep_ms = sweep_ms / args.steps
         kernel_name = f"walk_kernel<{kt}>"
+    elif fp32_launches > 0:
+        # dominant kernel: the FP32 correction pass (the Q1.63 passes only certify)
+        avg_sweep_ms = fp32_ms / fp32_launches
+        per_launch = fp32_pass_bytes(n, m, kt)
+        kernel_name = f"refine_pass_kernel<{kt}>"
     else:
         avg_sweep_ms = sweep_ms / max(sweep_launches, 1)
         per_launch = sweep_bytes(n, m, kt)
@@ -327,7 +350,8 @@ def run_gpu(args):
         "metric": METRIC_APPROX if approx else METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 push, u32 counts, f64 estimates" if approx else "int64 (Q1.63 fixed point), f64 output",
+        "dtype": "f32 push, u32 counts, f64 estimates" if approx else
+                 "f32 correction passes, int64 (Q1.63 fixed point) certifying passes, f64 output",
         "data": "synthetic",
         "config": {"workload": args.workload, "graph": f"R-MAT scale {WORKLOADS[args.workload][0]}, "
                    f"edge factor {WORKLOADS[args.workload][1]}, a/b/c/d 0.57/0.19/0.19/0.05",
@@ -339,7 +363,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": 8 * k * n},
         "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None if approx else ncu_traffic(args.workload),
+                     "traffic": None if approx else ncu_traffic(args.workload, kernel_name.split("<")[0]),
                      "algorithmic_bytes_per_launch": per_launch,
                      "avg_launch_ms": avg_sweep_ms},
         "cpu_baseline": cpu,

@@ -47,6 +47,11 @@ typedef enum {
 #define PPR_FLAG_SYNC 2    /* HP: every pass synchronous (SimFwdPush, equal to PowItr by Lemma 1);
                               by default passes run in place except the certifying last
                               pass of each batch (asynchronous updates, Sec. 5) */
+#define PPR_FLAG_FIXED_PASSES 8 /* HP: every pass in Q1.63.  By default the dense phase
+                              solves for the remaining error e = pi - X with FP32 passes,
+                              folds e into the Q1.63 estimate X and certifies with one
+                              exact synchronous Q1.63 pass (iterative refinement); the
+                              bound and its guarantee are the same either way */
 
 typedef enum {
   PPR_HP = 0,     /* high precision: ||pi_hat - pi||_1 <= lambda (PowerPush, Algorithm 3) */
@@ -92,6 +97,9 @@ typedef struct {
   int64_t kernel_launches;      /* kernels this call launched */
   int64_t sweep_launches;       /* of which sweep-kernel launches */
   double W;                     /* APPROX: walk budget of Eq. 8 (natural log) */
+  int32_t fp32_passes;          /* HP: of `sweeps`, FP32 correction passes (the rest are Q1.63) */
+  int32_t refine_cycles;        /* HP: fold + exact-pass cycles of the refinement */
+  double ms_fp32;               /* HP: device time of the FP32 passes (part of ms_sweep) */
 } ppr_stats;
 
 /* Fill opts with defaults: alpha 0.2, lambda 1e-8, eps 0.5, mu 0 (=1/n),

@@ -20,6 +20,7 @@ PPR_HP, PPR_APPROX = 0, 1
 PPR_FLAG_PARTIAL = 1
 PPR_FLAG_SYNC = 2
 PPR_FLAG_INDEX = 4
+PPR_FLAG_FIXED_PASSES = 8
 
 STATUS_NAMES = {0: "PPR_OK", -1: "PPR_ERR_ARG", -2: "PPR_ERR_GRAPH", -3: "PPR_ERR_OOM",
                 -4: "PPR_ERR_NOT_CONVERGED", -5: "PPR_ERR_CUDA", -6: "PPR_ERR_ADMIT"}
@@ -65,6 +66,9 @@ class ppr_stats(ctypes.Structure):
         ("kernel_launches", ctypes.c_int64),
         ("sweep_launches", ctypes.c_int64),
         ("W", ctypes.c_double),
+        ("fp32_passes", ctypes.c_int32),
+        ("refine_cycles", ctypes.c_int32),
+        ("ms_fp32", ctypes.c_double),
     ]
 
     def as_dict(self):

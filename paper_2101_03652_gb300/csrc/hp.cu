@@ -39,6 +39,7 @@
 #include "ppr_internal.cuh"
 #include "sweep_kernel.cuh"
 #include "epoch_kernel.cuh"
+#include "refine_kernel.cuh"
 
 namespace ppr {
 
@@ -404,6 +405,167 @@ static ppr_status run_epochs(ppr_graph* g, const ppr_graph::SweepPlan& plan, int
   return PPR_OK;
 }
 
+// State of one tile's sweep phase handed to the refinement driver.
+struct RefineTile {
+  int ncols;
+  double alpha, lambda;
+  int max_sweeps;
+  bool have_state;           // (r, pi) hold a push state; else r = e_s, pi = 0
+  std::vector<double> rsum;  // residue sums of the push state
+};
+
+// Sweep phase with FP32 correction passes (see refine_kernel.cuh).  Buffers:
+// pi = X (Q1.63 base); r = the push residue, then e of the FP32 passes, then
+// X' of the exact pass; zb = [r_f | z_e]; za = the second z_e buffer, then
+// z(X) for the exact pass.  Every stop is certified by an exact synchronous
+// pass: ||pi - X'||_1 <= (1-alpha) ||X' - X||_1 / alpha.  The answer is X' (r).
+template <int KT>
+static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int grid_ew, SweepArgs sa,
+                             const RefineTile& t, double* resid, u64* hpin, int& sweeps, int64_t& launches,
+                             std::vector<double>& bound, float& ms_sweep, int& fp32_passes, int& cycles,
+                             float& ms_fp32, cudaEvent_t es0, cudaEvent_t es1, cudaStream_t st) {
+  const int64_t n = g->n, m = g->m;
+  const size_t cells = (size_t)n * KT;
+  const int ncols = t.ncols;
+  const double alpha = t.alpha, lambda = t.lambda;
+  Workspace& ws = g->ws;
+  u64* X = ws.pi.as<u64>();
+  u64* Xn = ws.r.as<u64>();
+  u64* za = ws.za.as<u64>();
+  float* rf = ws.zb.as<float>();
+  float* ze_a = rf + cells;
+  float* ze_b = ws.za.as<float>();
+  float* ef = ws.r.as<float>();
+  const float oma = (float)(1.0 - alpha);
+
+  Plan* fplan = nullptr;
+  PPR_TRY(get_plan(g, Lay32<KT>::L, &fplan, st));
+  int bps = 0;
+  PPR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, refine_pass_kernel<KT>, 256, 0));
+  const int fgrid = sm_count() * std::max(bps, 1);
+  RefArgs ra;
+  ra.items = fplan->d_items;
+  ra.in_rp = g->d_in_rp;
+  ra.in_ci = g->d_in_ci;
+  ra.deg = g->d_deg;
+  ra.rf = rf;
+  ra.one_minus_alpha = oma;
+  ra.npieces = fplan->d_npieces;
+  ra.heavy_acc = ws.heavy_acc.as<float>();
+  ra.heavy_cnt = ws.heavy_cnt.as<unsigned int>();
+
+  // cycle 0: X = reserve, r = alpha r_push
+  double F0 = 0.0;  // ||r||_1 of the cycle = ||e_1 - e_0||_1
+  for (int c = 0; c < ncols; ++c) F0 = std::max(F0, alpha * (t.have_state ? t.rsum[c] : 1.0));
+  refine_setup_push_kernel<KT><<<grid_ew, 256, 0, st>>>(n, Xn, alpha, g->d_deg, oma, rf, ze_a);
+  ++launches;
+  const double slack = (double)m * 0.5 / kFixOne / alpha;
+  // FP32 goal: after the fold the exact pass measures ||X' - X||_1 of about
+  // (1-alpha) F (F = the last measured ||e' - e||_1), so the certified bound
+  // comes out near (1-alpha)^2 F / alpha; aim at 0.6 lambda
+  const double target_f = 0.6 * lambda * alpha / ((1.0 - alpha) * (1.0 - alpha));
+  double rate = -1.0;  // observed contraction per FP32 pass
+  for (int cycle = 0;; ++cycle) {
+    if (cycle >= 8) {
+      set_error("refinement did not certify within 8 cycles");
+      return PPR_ERR_NOT_CONVERGED;
+    }
+    // ---- FP32 passes: in place, the last of each batch synchronous, measured,
+    // and writing e for the fold
+    const double goal = std::max(target_f, 1e-6 * F0);  // FP32 sums stop contracting near 1e-6 F0
+    double F = F0;
+    float* zcur = ze_a;
+    float* znext = ze_b;
+    while (F > goal) {
+      const double cr = rate > 0.0 ? rate : (1.0 - alpha);
+      int S = std::max((int)std::ceil(std::log(goal / F) / std::log(cr) - 1e-12), 1);
+      if (rate <= 0.0) S = std::min(S, 16);  // learn the rate first
+      if (sweeps + S + 1 > t.max_sweeps) {
+        set_error("sweep limit %d reached", t.max_sweeps);
+        return PPR_ERR_NOT_CONVERGED;
+      }
+      PPR_CUDA_TRY(cudaMemsetAsync(resid, 0, 64 * 8, st));
+      PPR_CUDA_TRY(cudaEventRecord(es0, st));
+      for (int j = 0; j < S; ++j) {
+        const bool last = j == S - 1;
+        ra.ze_in = zcur;
+        ra.ze_out = last ? znext : zcur;
+        ra.e_out = last ? ef : nullptr;
+        ra.resid = last ? resid : nullptr;
+        // rows without in-edges keep z_e = r_f (1-alpha)/d from the setup; the
+        // synchronous pass rewrites every row of the other buffer
+        ra.n_items = last ? fplan->n_items_all : fplan->n_items_nz;
+        refine_pass_kernel<KT><<<fgrid, 256, 0, st>>>(ra);
+      }
+      PPR_CUDA_TRY(cudaEventRecord(es1, st));
+      PPR_CUDA_TRY(cudaGetLastError());
+      std::swap(zcur, znext);
+      sweeps += S;
+      fp32_passes += S;
+      launches += S;
+      PPR_CUDA_TRY(cudaMemcpyAsync(hpin, resid, 64 * 8, cudaMemcpyDeviceToHost, st));
+      PPR_CUDA_TRY(cudaStreamSynchronize(st));
+      float a_ms = 0.f;
+      cudaEventElapsedTime(&a_ms, es0, es1);
+      ms_sweep += a_ms;
+      ms_fp32 += a_ms;
+      const double* D = reinterpret_cast<const double*>(hpin);
+      double Fm = 0.0;
+      for (int c = 0; c < ncols; ++c) Fm = std::max(Fm, D[c]);
+      if (!(Fm >= 0.0) || !std::isfinite(Fm)) {
+        set_error("FP32 correction passes diverged");
+        return PPR_ERR_NOT_CONVERGED;
+      }
+      if (Fm > 0.0 && Fm < F && S >= 2)
+        rate = std::min(1.0 - alpha, std::max(0.05, std::pow(Fm / F, 1.0 / S)));
+      const bool stalled = S >= 3 && Fm > 0.7 * F;
+      F = Fm;
+      if (stalled) break;
+    }
+    if (F == F0) {
+      // nothing ran (r already below the goal): e = r
+      PPR_CUDA_TRY(cudaMemcpyAsync(ef, rf, cells * 4, cudaMemcpyDeviceToDevice, st));
+    }
+
+    // ---- fold e into X, one exact synchronous pass from X
+    refine_fold_kernel<KT><<<grid_ew, 256, 0, st>>>(n, ef, X, g->d_omega, za);
+    ++launches;
+    PPR_CUDA_TRY(cudaMemsetAsync(resid, 0, 64 * 8, st));
+    sa.z_in = za;
+    sa.z_out = nullptr;
+    sa.x_out = Xn;
+    sa.n_items = plan.n_items_all;
+    sa.resid = resid;
+    PPR_CUDA_TRY(cudaEventRecord(es0, st));
+    sweep_kernel<KT><<<sweep_grid, 256, 0, st>>>(sa);
+    PPR_CUDA_TRY(cudaEventRecord(es1, st));
+    PPR_CUDA_TRY(cudaGetLastError());
+    ++sweeps;
+    ++launches;
+    ++cycles;
+    PPR_CUDA_TRY(cudaMemcpyAsync(hpin, resid, 64 * 8, cudaMemcpyDeviceToHost, st));
+    PPR_CUDA_TRY(cudaStreamSynchronize(st));
+    {
+      float a_ms = 0.f;
+      cudaEventElapsedTime(&a_ms, es0, es1);
+      ms_sweep += a_ms;
+    }
+    const double* D = reinterpret_cast<const double*>(hpin);
+    bool ok = true;
+    F0 = 0.0;
+    for (int c = 0; c < ncols; ++c) {
+      const double Dc = D[c] / kFixOne / alpha;  // ||X' - X||_1 / alpha
+      bound[c] = (1.0 - alpha) * Dc * (1.0 + 1e-4) + 2.0 * slack;
+      if (bound[c] > lambda) ok = false;
+      F0 = std::max(F0, Dc * alpha);
+    }
+    if (ok) return PPR_OK;
+    // next cycle from X: r = X' - X
+    refine_setup_resid_kernel<KT><<<grid_ew, 256, 0, st>>>(n, Xn, X, g->d_deg, oma, rf, ze_a);
+    ++launches;
+  }
+}
+
 template <int KT>
 static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query_opts& o, double* out_pi,
                          double* out_r, ppr_stats* stats, cudaStream_t st) {
@@ -502,7 +664,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
   PPR_CUDA_TRY(cudaEventCreate(&ev2));
   PPR_CUDA_TRY(cudaEventCreate(&es0));
   PPR_CUDA_TRY(cudaEventCreate(&es1));
-  float ms_push = 0.f, ms_sweep = 0.f, ms_total = 0.f;
+  float ms_push = 0.f, ms_sweep = 0.f, ms_total = 0.f, ms_fp32 = 0.f;
   int64_t launches = 0, sweep_launches = 0;
 
   ppr_status status = PPR_OK;
@@ -524,6 +686,8 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
     const int corr = o.warm_start ? warm_correction_passes(o.warm_start) : 0;
     const bool warm = o.warm_start != nullptr && corr == 0;
     const bool partial = (o.flags & PPR_FLAG_PARTIAL) != 0;
+    const bool refine = o.warm_start == nullptr && !partial &&
+                        (o.flags & (PPR_FLAG_SYNC | PPR_FLAG_FIXED_PASSES)) == 0;
     bool corrected = false;
     if (switch_edges != 0 && !warm) {
       PPR_CUDA_TRY(cudaMemsetAsync(r, 0, cells * 8, st));
@@ -585,7 +749,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
     PPR_CUDA_TRY(cudaEventRecord(ev1, st));
 
     // ---- sweep phase
-    int sweeps = 0;
+    int sweeps = 0, fp32_passes = 0, refine_cycles = 0;
     std::vector<double> bound(KT, 0.0);
     u64* xfinal = pi;  // the estimate to output
     bool need_dense = !all_done;
@@ -613,6 +777,47 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
       xfinal = pi;
       if (out_r)
         output_kernel<KT><<<grid_ew, 256, 0, st>>>(n, g->d_new_of_old, r, ncols, t0, out_r_dev), ++launches;
+    } else if (refine) {
+      // FP32 correction passes certified by exact passes (the default solve)
+      if (!have_state) {
+        PPR_CUDA_TRY(cudaMemsetAsync(r, 0, cells * 8, st));
+        PPR_CUDA_TRY(cudaMemsetAsync(pi, 0, cells * 8, st));
+        PPR_CUDA_TRY(cudaMemcpyAsync(d_src, src_new, sizeof(src_new), cudaMemcpyHostToDevice, st));
+        init_sources_kernel<KT><<<1, 64, 0, st>>>(d_src, ncols, r, ws.stamp.as<uint32_t>(), ++g->stamp_epoch,
+                                                  ws.front_a.as<uint32_t>());
+        ++launches;
+        for (int c = 0; c < KT; ++c) r0[c] = 1.0;
+      }
+      SweepArgs sa;
+      sa.items = plan.d_items;
+      sa.in_rp = g->d_in_rp;
+      sa.in_ci = g->d_in_ci;
+      sa.omega = g->d_omega;
+      sa.invw = g->d_invw;
+      sa.alpha_raw = alpha_raw;
+      for (int c = 0; c < 64; ++c) sa.src[c] = src_new[c];
+      sa.heavy_npieces = plan.d_npieces;
+      sa.heavy_acc = ws.heavy_acc.as<u64>();
+      sa.heavy_cnt = ws.heavy_cnt.as<unsigned int>();
+      RefineTile rt;
+      rt.ncols = ncols;
+      rt.alpha = alpha;
+      rt.lambda = lambda;
+      rt.max_sweeps = max_sweeps;
+      rt.have_state = have_state;
+      rt.rsum = rsum;
+      status = run_refine<KT>(g, plan, sweep_grid, grid_ew, sa, rt, resid, hpin, sweeps, launches, bound, ms_sweep,
+                              fp32_passes, refine_cycles, ms_fp32, es0, es1, st);
+      if (status != PPR_OK) break;
+      sweep_launches += sweeps;
+      xfinal = r;
+      if (out_r) {
+        // residual of the returned estimate: one more gather over z(X')
+        z_of_x_kernel<KT><<<grid_ew, 256, 0, st>>>(n, r, g->d_omega, za);
+        residual_kernel<KT><<<grid_ew, 256, 0, st>>>((int32_t)n, g->d_in_rp, g->d_in_ci, g->d_old_of_new, za, r, sa,
+                                                     ncols, t0, alpha, out_r_dev);
+        launches += 2;
+      }
     } else {
       if (warm) {
         // x0 from the model; its residual norm is measured by the first pass
@@ -776,6 +981,8 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
         s.initial_l1_residual = need_dense ? r0[c] : rsum[c];
         s.final_l1_residual = bound[c];
         s.mass_deficit = 1.0 - (double)hpin[c] / kFixOne;
+        s.fp32_passes = fp32_passes;
+        s.refine_cycles = refine_cycles;
       }
     }
   }
@@ -791,6 +998,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
       stats[i].ms_push = ms_push;
       stats[i].ms_sweep = ms_sweep;
       stats[i].ms_total = ms_total;
+      stats[i].ms_fp32 = ms_fp32;
       stats[i].kernel_launches = launches;
       stats[i].sweep_launches = sweep_launches;
     }

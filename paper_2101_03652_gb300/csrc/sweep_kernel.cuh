@@ -28,7 +28,7 @@ struct SweepArgs {
   const uint64_t* omega;
   const float* invw;
   const u64* z_in;
-  u64* z_out;
+  u64* z_out;        // NULL: z of this pass not stored (a measuring pass)
   u64* x_out;        // optional: the estimate x of this pass
   int32_t src[64];   // tile's sources (new ids), -1 for unused columns
   u64 alpha_raw;     // alpha in Q1.63
@@ -88,7 +88,7 @@ __device__ __forceinline__ void row_epilogue(const SweepArgs& a, int u, int slot
 #pragma unroll
     for (int q = 0; q < V; ++q) res[q] += (float)(zn[q] > zo[q] ? zn[q] - zo[q] : zo[q] - zn[q]) * iw;
   }
-  st_vec<V>(a.z_out + (size_t)u * KT + slot * V, zn);
+  if (a.z_out) st_vec<V>(a.z_out + (size_t)u * KT + slot * V, zn);
   if (a.x_out) st_vec<V>(a.x_out + (size_t)u * KT + slot * V, xn);
 }
 

@@ -225,9 +225,43 @@ def test_asynchronous_passes_need_fewer_than_powitr(P, c0, c0_ref):
     """Default in-place passes (asynchronous updates) certify the same bound
     with fewer passes than the synchronous ones."""
     rp, ci, src = c0
-    pi, st = run(P, rp, ci, src, switch_edges=0)
-    pi_s, st_s = run(P, rp, ci, src, switch_edges=0, flags=2)
+    pi, st = run(P, rp, ci, src, switch_edges=0, flags=P.PPR_FLAG_FIXED_PASSES)
+    pi_s, st_s = run(P, rp, ci, src, switch_edges=0, flags=P.PPR_FLAG_SYNC)
     for i, s in enumerate(src):
         assert np.abs(pi[i] - c0_ref[int(s)]).sum() <= 2 * LAM
     check_bound_and_mass(st)
     assert st[0]["sweeps"] < st_s[0]["sweeps"] == 83
+
+
+@pytest.mark.parametrize("k_tile,switch", [(1, -1), (8, 0), (16, -1), (64, -1)])
+def test_fp32_refinement_is_certified(P, c0, c0_ref, k_tile, switch):
+    """Default dense phase (FP32 correction passes folded into the Q1.63
+    estimate, stop certified by an exact pass) against the oracle and against
+    the all-Q1.63 passes: both within 2 lambda of the oracle, bound certified."""
+    rp, ci, src = c0
+    pi, st = run(P, rp, ci, src, k_tile=k_tile, switch_edges=switch)
+    pi_f, st_f = run(P, rp, ci, src, k_tile=k_tile, switch_edges=switch, flags=P.PPR_FLAG_FIXED_PASSES)
+    for i, s in enumerate(src):
+        assert np.abs(pi[i] - c0_ref[int(s)]).sum() <= 2 * LAM
+        assert np.abs(pi_f[i] - c0_ref[int(s)]).sum() <= 2 * LAM
+    check_bound_and_mass(st)
+    assert np.all(pi >= 0)
+    print(f"k_tile {k_tile}: passes refine {st[0]['sweeps']} fixed {st_f[0]['sweeps']}")
+
+
+def test_fp32_refinement_residual_output(P, c0, c0_ref):
+    """out_r of a refined answer: the residual of the returned estimate."""
+    rp, ci, src = c0
+    g = P.Graph(rp, ci)
+    n = len(rp) - 1
+    out = np.zeros((3, n))
+    out_r = np.zeros((3, n))
+    _, st = g.query(src[:3], P.PPR_HP, out_pi=out, out_r=out_r, lam=LAM, k_tile=4)
+    g.close()
+    og = O.Graph(rp, ci)
+    for i, s in enumerate(src[:3]):
+        assert np.abs(out[i] - c0_ref[int(s)]).sum() <= 2 * LAM
+        # the residual of the returned estimate, recomputed by the oracle's definition
+        ref_r = O.residual(og, int(s), out[i], ALPHA)
+        assert np.abs(out_r[i] - ref_r).sum() <= 1e-12 + 1e-6 * np.abs(ref_r).sum()
+        assert np.abs(out_r[i]).sum() <= st[i]["final_l1_residual"]
