@@ -33,6 +33,14 @@ struct RefArgs {
   double* resid;       // [KT] sums of |e_new - e_old| (NULL: not measured)
 };
 
+// gathers in flight per lane and blocks per SM: wide tiles keep more gathers
+// per warp; narrow ones more warps (measured on R-MAT scale 20)
+template <int KT>
+struct RefTune {
+  static constexpr int UNR = KT >= 32 ? 8 : 4;
+  static constexpr int MIN_BLOCKS = KT >= 32 ? 6 : 8;
+};
+
 template <int V>
 __device__ __forceinline__ void stf(float* p, const float (&v)[V]) {
   if constexpr (V == 4) {
@@ -73,7 +81,7 @@ __device__ __forceinline__ void refine_epilogue(const RefArgs& a, int u, int slo
 template <int KT>
 __device__ __forceinline__ void refine_gather_warp(const RefArgs& a, int e_begin, int e_end, int lane, int slot,
                                                    float (&acc)[Lay32<KT>::V]) {
-  constexpr int V = Lay32<KT>::V, L = Lay32<KT>::L, EPW = Lay32<KT>::EPW, UNR = kUnr;
+  constexpr int V = Lay32<KT>::V, L = Lay32<KT>::L, EPW = Lay32<KT>::EPW, UNR = RefTune<KT>::UNR;
   for (int base = e_begin; base < e_end; base += EPW * UNR) {
     int v[UNR];
 #pragma unroll
@@ -99,7 +107,7 @@ __device__ __forceinline__ void refine_gather_warp(const RefArgs& a, int e_begin
 }
 
 template <int KT>
-__global__ void __launch_bounds__(256, 6) refine_pass_kernel(RefArgs a) {
+__global__ void __launch_bounds__(256, RefTune<KT>::MIN_BLOCKS) refine_pass_kernel(RefArgs a) {
   constexpr int V = Lay32<KT>::V, L = Lay32<KT>::L;
   const int lane = threadIdx.x & 31;
   const int slot = lane % L;
@@ -149,7 +157,7 @@ __global__ void __launch_bounds__(256, 6) refine_pass_kernel(RefArgs a) {
       for (int u = w.y + lane / L; u < w.z; u += 32 / L) {
         const int e1 = __ldg(&a.in_rp[u + 1]);
         float acc[V] = {};
-#pragma unroll 4
+#pragma unroll RefTune<KT>::UNR
         for (int e = __ldg(&a.in_rp[u]); e < e1; ++e) {
           float t[V];
           ldf<V>(a.ze_in + (size_t)__ldg(&a.in_ci[e]) * KT + slot * V, t);
