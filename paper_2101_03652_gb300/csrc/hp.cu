@@ -412,6 +412,13 @@ struct RefineTile {
   int max_sweeps;
   bool have_state;           // (r, pi) hold a push state; else r = e_s, pi = 0
   std::vector<double> rsum;  // residue sums of the push state
+  // learned estimate: with correction_passes L = 0 it replaces the start (X =
+  // the model's estimate, first measured by an exact pass); with L > 0 the
+  // remaining mass is added as mu q after the first L FP32 passes
+  const void* model = nullptr;
+  int corr = 0;
+  const int32_t* src_new = nullptr;
+  u64* mass = nullptr;       // [KT] device scratch for exact column sums
 };
 
 // Sweep phase with FP32 correction passes (see refine_kernel.cuh).  Buffers:
@@ -422,8 +429,9 @@ struct RefineTile {
 template <int KT>
 static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int grid_ew, SweepArgs sa,
                              const RefineTile& t, double* resid, u64* hpin, int& sweeps, int64_t& launches,
-                             std::vector<double>& bound, float& ms_sweep, int& fp32_passes, int& cycles,
-                             float& ms_fp32, cudaEvent_t es0, cudaEvent_t es1, cudaStream_t st) {
+                             std::vector<double>& bound, std::vector<double>& r0, float& ms_sweep,
+                             int& fp32_passes, int& cycles, float& ms_fp32, cudaEvent_t es0, cudaEvent_t es1,
+                             cudaStream_t st) {
   const int64_t n = g->n, m = g->m;
   const size_t cells = (size_t)n * KT;
   const int ncols = t.ncols;
@@ -454,11 +462,19 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
   ra.heavy_acc = ws.heavy_acc.as<float>();
   ra.heavy_cnt = ws.heavy_cnt.as<unsigned int>();
 
-  // cycle 0: X = reserve, r = alpha r_push
   double F0 = 0.0;  // ||r||_1 of the cycle = ||e_1 - e_0||_1
-  for (int c = 0; c < ncols; ++c) F0 = std::max(F0, alpha * (t.have_state ? t.rsum[c] : 1.0));
-  refine_setup_push_kernel<KT><<<grid_ew, 256, 0, st>>>(n, Xn, alpha, g->d_deg, oma, rf, ze_a);
-  ++launches;
+  const bool warm_x0 = t.model && t.corr == 0;
+  bool corr_pending = t.model && t.corr > 0;
+  if (warm_x0) {
+    // X = the model's estimate; the first exact pass measures its residual
+    PPR_TRY(warm_start_tile(t.model, g, t.src_new, ncols, KT, alpha, za, X, st));
+    ++launches;
+  } else {
+    // cycle 0: X = reserve, r = alpha r_push
+    for (int c = 0; c < ncols; ++c) F0 = std::max(F0, alpha * (t.have_state ? t.rsum[c] : 1.0));
+    refine_setup_push_kernel<KT><<<grid_ew, 256, 0, st>>>(n, Xn, alpha, g->d_deg, oma, rf, ze_a);
+    ++launches;
+  }
   const double slack = (double)m * 0.5 / kFixOne / alpha;
   // FP32 goal: after the fold the exact pass measures ||X' - X||_1 of about
   // (1-alpha) F (F = the last measured ||e' - e||_1), so the certified bound
@@ -476,10 +492,11 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
     double F = F0;
     float* zcur = ze_a;
     float* znext = ze_b;
-    while (F > goal) {
+    while (!(warm_x0 && cycle == 0) && F > goal) {
       const double cr = rate > 0.0 ? rate : (1.0 - alpha);
       int S = std::max((int)std::ceil(std::log(goal / F) / std::log(cr) - 1e-12), 1);
       if (rate <= 0.0) S = std::min(S, 16);  // learn the rate first
+      if (corr_pending) S = t.corr;          // the passes the correction model was trained after
       if (sweeps + S + 1 > t.max_sweeps) {
         set_error("sweep limit %d reached", t.max_sweeps);
         return PPR_ERR_NOT_CONVERGED;
@@ -520,16 +537,28 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
         rate = std::min(1.0 - alpha, std::max(0.05, std::pow(Fm / F, 1.0 / S)));
       const bool stalled = S >= 3 && Fm > 0.7 * F;
       F = Fm;
-      if (stalled) break;
+      if (stalled || corr_pending) break;
     }
-    if (F == F0) {
-      // nothing ran (r already below the goal): e = r
-      PPR_CUDA_TRY(cudaMemcpyAsync(ef, rf, cells * 4, cudaMemcpyDeviceToDevice, st));
+    if (!(warm_x0 && cycle == 0)) {
+      if (F == F0) {
+        // nothing ran (r already below the goal): e = r
+        PPR_CUDA_TRY(cudaMemcpyAsync(ef, rf, cells * 4, cudaMemcpyDeviceToDevice, st));
+      }
+      // ---- fold e into X (z(X) to za)
+      refine_fold_kernel<KT><<<grid_ew, 256, 0, st>>>(n, ef, X, g->d_omega, za);
+      ++launches;
+      if (corr_pending) {
+        // X += mu q (mu = 1 - sum X, exact), z(X) rewritten
+        PPR_CUDA_TRY(cudaMemsetAsync(t.mass, 0, 8 * KT, st));
+        column_sum_kernel<KT><<<grid_ew, 256, 0, st>>>(n, X, t.mass);
+        PPR_TRY(warm_correct_tile(t.model, g, t.src_new, ncols, KT, alpha, X, t.mass, za, X, st));
+        launches += 2;
+        corr_pending = false;
+        rate = -1.0;  // the correction changes the error: learn the rate again
+      }
     }
 
-    // ---- fold e into X, one exact synchronous pass from X
-    refine_fold_kernel<KT><<<grid_ew, 256, 0, st>>>(n, ef, X, g->d_omega, za);
-    ++launches;
+    // ---- one exact synchronous pass from X
     PPR_CUDA_TRY(cudaMemsetAsync(resid, 0, 64 * 8, st));
     sa.z_in = za;
     sa.z_out = nullptr;
@@ -558,6 +587,7 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
       bound[c] = (1.0 - alpha) * Dc * (1.0 + 1e-4) + 2.0 * slack;
       if (bound[c] > lambda) ok = false;
       F0 = std::max(F0, Dc * alpha);
+      if (warm_x0 && cycle == 0) r0[c] = Dc;  // measured ||r(x0)||_1 of the model's estimate
     }
     if (ok) return PPR_OK;
     // next cycle from X: r = X' - X
@@ -686,8 +716,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
     const int corr = o.warm_start ? warm_correction_passes(o.warm_start) : 0;
     const bool warm = o.warm_start != nullptr && corr == 0;
     const bool partial = (o.flags & PPR_FLAG_PARTIAL) != 0;
-    const bool refine = o.warm_start == nullptr && !partial &&
-                        (o.flags & (PPR_FLAG_SYNC | PPR_FLAG_FIXED_PASSES)) == 0;
+    const bool refine = !partial && (o.flags & (PPR_FLAG_SYNC | PPR_FLAG_FIXED_PASSES)) == 0;
     bool corrected = false;
     if (switch_edges != 0 && !warm) {
       PPR_CUDA_TRY(cudaMemsetAsync(r, 0, cells * 8, st));
@@ -806,8 +835,12 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
       rt.max_sweeps = max_sweeps;
       rt.have_state = have_state;
       rt.rsum = rsum;
-      status = run_refine<KT>(g, plan, sweep_grid, grid_ew, sa, rt, resid, hpin, sweeps, launches, bound, ms_sweep,
-                              fp32_passes, refine_cycles, ms_fp32, es0, es1, st);
+      rt.model = o.warm_start;
+      rt.corr = corr;
+      rt.src_new = src_new;
+      rt.mass = mass;
+      status = run_refine<KT>(g, plan, sweep_grid, grid_ew, sa, rt, resid, hpin, sweeps, launches, bound, r0,
+                              ms_sweep, fp32_passes, refine_cycles, ms_fp32, es0, es1, st);
       if (status != PPR_OK) break;
       sweep_launches += sweeps;
       xfinal = r;
@@ -822,7 +855,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
       if (warm) {
         // x0 from the model; its residual norm is measured by the first pass
         PPR_CUDA_TRY(cudaMemsetAsync(za, 0, cells * 8, st));
-        PPR_TRY(warm_start_tile(o.warm_start, g, src_new, ncols, KT, alpha, za, st));
+        PPR_TRY(warm_start_tile(o.warm_start, g, src_new, ncols, KT, alpha, za, nullptr, st));
         for (int c = 0; c < KT; ++c) r0[c] = std::numeric_limits<double>::infinity();
       } else if (have_state) {
         convert_kernel<KT><<<grid_ew, 256, 0, st>>>(n, r, pi, g->d_omega, alpha64, za);
@@ -932,7 +965,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
           // the residual's sum becomes zero and its norm is measured again
           PPR_CUDA_TRY(cudaMemsetAsync(mass, 0, 8 * KT, st));
           column_sum_kernel<KT><<<grid_ew, 256, 0, st>>>(n, r, mass);
-          PPR_TRY(warm_correct_tile(o.warm_start, g, src_new, ncols, KT, alpha, r, mass, zcur, st));
+          PPR_TRY(warm_correct_tile(o.warm_start, g, src_new, ncols, KT, alpha, r, mass, zcur, nullptr, st));
           launches += 1;
           corrected = true;
           R = std::numeric_limits<double>::infinity();

@@ -114,12 +114,14 @@ ppr_status query_approx(ppr_graph* g, const int32_t* src, int32_t k, const ppr_q
 bool is_device_pointer(const void* p);
 ppr_status get_plan(ppr_graph* g, int lanes, ppr_graph::SweepPlan** out, cudaStream_t st);
 int sm_count();
+// z0 (and x0 when not NULL) of the model's estimate for a solver tile
 ppr_status warm_start_tile(const void* model, ppr_graph* g, const int32_t* src_new, int ncols, int kt, double alpha,
-                           unsigned long long* z0, cudaStream_t st);
+                           unsigned long long* z0, unsigned long long* x0, cudaStream_t st);
 int warm_correction_passes(const void* model);
 int64_t hp_state_bytes(const ppr_graph* g, int32_t k, int32_t kt);
 int tune_bucket(int32_t k);
+// x + mu q with mu = 1 - sum x: z of it, and the corrected x when x_out is not NULL
 ppr_status warm_correct_tile(const void* model, ppr_graph* g, const int32_t* src_new, int ncols, int kt, double alpha,
                              const unsigned long long* x, const unsigned long long* mass, unsigned long long* z,
-                             cudaStream_t st);
+                             unsigned long long* x_out, cudaStream_t st);
 }  // namespace ppr

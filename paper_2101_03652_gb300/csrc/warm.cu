@@ -262,6 +262,7 @@ struct BasisArgs {
   int with_sketch;      // Z = S + U h (1) or Z = U h (0: the model predicts a distribution)
   const u64* xin;       // pass 6: current estimate [n][kt] (Q1.63)
   const u64* mass;      // pass 6: [kt] exact sums of xin
+  u64* xout;            // passes 4 and 6: the estimate itself (Q1.63), if not NULL
 };
 
 template <int B, int PASS>
@@ -318,17 +319,23 @@ __global__ void __launch_bounds__(256) basis_kernel(BasisArgs a) {
             const u64 xf = (u64)((double)X * kFixOne);
             const u64 om = a.omega[u];
             const u64 hi = __umul64hi(xf, om), lo = xf * om;
-            if (c < a.kt) a.z0[(size_t)u * a.kt + c] = hi + (lo >> 63);
+            if (c < a.kt) {
+              a.z0[(size_t)u * a.kt + c] = hi + (lo >> 63);
+              if (a.xout) a.xout[(size_t)u * a.kt + c] = xf;
+            }
           } else if constexpr (PASS == 5) {
             a.Xout[(size_t)u * B + c] = X;
           } else if constexpr (PASS == 6) {
-            // x += mu X with mu = 1 - sum x (exact, raw units); z = x (1-alpha)/d
+            // x += mu X with mu = 1 - sum x (exact, raw units; no correction when
+            // the estimate already holds all the mass); z = x (1-alpha)/d
             if (c < a.kt) {
-              const u64 mu = kFixOneRaw - a.mass[c];
-              const u64 xn = a.xin[(size_t)u * a.kt + c] + (u64)((double)mu * (double)X);
+              const long long mu = (long long)(kFixOneRaw - a.mass[c]);
+              const u64 add = mu > 0 ? (u64)((double)mu * (double)X) : 0ull;
+              const u64 xn = a.xin[(size_t)u * a.kt + c] + add;
               const u64 om = a.omega[u];
               const u64 hi = __umul64hi(xn, om), lo = xn * om;
               a.z0[(size_t)u * a.kt + c] = hi + (lo >> 63);
+              if (a.xout) a.xout[(size_t)u * a.kt + c] = xn;
             }
           } else {
             const float diff = X - a.pi[(size_t)u * a.ldpi + c];
@@ -685,12 +692,13 @@ static ppr_status model_estimate_internal(ppr_model* md, const int32_t* src_new_
 
 // initial estimate for a solver tile: z0[u * kt + c] = x0 (1-alpha) / d_u in Q1.63
 ppr_status warm_start_tile(const void* model, ppr_graph* g, const int32_t* src_new, int ncols, int kt, double alpha,
-                           unsigned long long* z0, cudaStream_t st) {
+                           unsigned long long* z0, unsigned long long* x0, cudaStream_t st) {
   ppr_model* md = (ppr_model*)model;
   if (md->g != g) { set_error("warm_start model belongs to another graph"); return PPR_ERR_ARG; }
   PPR_TRY(ensure_alpha(g, alpha, st));
   BasisArgs ba = basis_args(md, ncols);
   ba.z0 = z0;
+  ba.xout = x0;
   ba.kt = kt;
   ba.omega = g->d_omega;
   const int grid = sm_count() * 4;
@@ -713,11 +721,12 @@ int warm_correction_passes(const void* model) { return ((const ppr_model*)model)
 // x + mu q for a solver tile, written as z = (x + mu q)(1-alpha)/d into z
 ppr_status warm_correct_tile(const void* model, ppr_graph* g, const int32_t* src_new, int ncols, int kt,
                              double alpha, const unsigned long long* x, const unsigned long long* mass,
-                             unsigned long long* z, cudaStream_t st) {
+                             unsigned long long* z, unsigned long long* x_out, cudaStream_t st) {
   ppr_model* md = (ppr_model*)model;
   if (md->g != g) { set_error("warm_start model belongs to another graph"); return PPR_ERR_ARG; }
   BasisArgs ba = basis_args(md, ncols);
   ba.z0 = z;
+  ba.xout = x_out;
   ba.kt = kt;
   ba.omega = g->d_omega;
   ba.xin = x;
