@@ -519,13 +519,61 @@ def run_serve(args):
     g.close()
 
 
+def run_eps_sweep(args):
+    """Accuracy study of SpeedPPR over eps (the methodology of Sec. 8's
+    accuracy experiments on synthetic inputs): for each eps, queries/s with
+    walks and with the index, the mean l1 error against certified
+    lambda = 1e-8 answers of the same sources, and the share of entries with
+    pi >= 1/n whose relative error exceeds eps."""
+    import numpy as np
+    import torch
+    import ppr_inputs as gen
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2101_03652_gb300 as P
+    rp, ci = gen.rmat(args.sweep_scale, 16, seed=1)
+    n, m = len(rp) - 1, len(ci)
+    src = gen.sources(n, 16, seed=3)
+    g = P.Graph(rp, ci)
+    exact, st_hp = g.query(src, P.PPR_HP, lam=LAMBDA, alpha=ALPHA)
+    assert max(x["final_l1_residual"] for x in st_hp) <= LAMBDA
+    exact = exact.cpu().numpy()
+    g.build_index(0x1DE5, ALPHA)
+    out = torch.empty((len(src), n), dtype=torch.float64, device="cuda")
+    rows = []
+    for eps in (0.1, 0.2, 0.3, 0.4, 0.5):
+        rec = {"eps": eps}
+        for name, flags in (("walks", 0), ("index", P.PPR_FLAG_INDEX)):
+            g.query(src, P.PPR_APPROX, out_pi=out, eps=eps, alpha=ALPHA, flags=flags)  # warm-up
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            _, st = g.query(src, P.PPR_APPROX, out_pi=out, eps=eps, alpha=ALPHA, flags=flags)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+            est = out.cpu().numpy()
+            big = exact >= 1.0 / n
+            rel = np.abs(est - exact)[big] / exact[big]
+            rec[name] = {"queries_per_s": len(src) / dt, "walks_per_source": float(np.mean([x["walks"] for x in st])),
+                         "mean_l1_error": float(np.abs(est - exact).sum(axis=1).mean()),
+                         "max_rel_error_pi_ge_1_over_n": float(rel.max()),
+                         "share_rel_error_above_eps": float((rel > eps).mean())}
+        rows.append(rec)
+    g.close()
+    print(json.dumps({"metric": "SpeedPPR accuracy over eps", "unit": "see rows", "data": "synthetic",
+                      "config": {"workload": "eps-sweep", "graph": f"R-MAT scale {args.sweep_scale}, edge factor 16",
+                                 "n": n, "m": m, "alpha": ALPHA, "sources": len(src), "mu": "1/n",
+                                 "reference": "HP answers certified at lambda = 1e-8"},
+                      "rows": rows}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat20-k64", choices=sorted(WORKLOADS) + ["serve"])
+    ap.add_argument("--workload", default="rmat20-k64", choices=sorted(WORKLOADS) + ["serve", "eps-sweep"])
+    ap.add_argument("--sweep-scale", type=int, default=20, help="R-MAT scale of the eps-sweep study")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the oracle CPU baseline")
     ap.add_argument("--skip-warm", action="store_true", help="omit the learned warm-start comparison")
     ap.add_argument("--serve-scale", type=int, default=25, help="R-MAT scale of the serving workload")
@@ -535,6 +583,8 @@ def main():
     args = ap.parse_args()
     if args.workload == "serve":
         run_serve(args)
+    elif args.workload == "eps-sweep":
+        run_eps_sweep(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

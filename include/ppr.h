@@ -47,6 +47,13 @@ typedef enum {
 #define PPR_FLAG_SYNC 2    /* HP: every pass synchronous (SimFwdPush, equal to PowItr by Lemma 1);
                               by default passes run in place except the certifying last
                               pass of each batch (asynchronous updates, Sec. 5) */
+#define PPR_FLAG_NO_ACTIVE 16 /* HP, with epoch_num > 0: end in a state where no node is
+                              active w.r.t. r_max = lambda/m (the Remark after Algorithm 3):
+                              the queue phase runs until its frontier is empty instead of
+                              stopping at sum r <= lambda, and after the epochs thresholded
+                              passes at lambda/m continue until no node is active.  With a
+                              switch_edges that no level reaches, the call is FIFO-FwdPush
+                              (Algorithm 2) by levels on the GPU */
 #define PPR_FLAG_FIXED_PASSES 8 /* HP: every pass in Q1.63.  By default the dense phase
                               solves for the remaining error e = pi - X with FP32 passes,
                               folds e into the Q1.63 estimate X and certifies with one

@@ -21,6 +21,7 @@ PPR_FLAG_PARTIAL = 1
 PPR_FLAG_SYNC = 2
 PPR_FLAG_INDEX = 4
 PPR_FLAG_FIXED_PASSES = 8
+PPR_FLAG_NO_ACTIVE = 16
 
 STATUS_NAMES = {0: "PPR_OK", -1: "PPR_ERR_ARG", -2: "PPR_ERR_GRAPH", -3: "PPR_ERR_OOM",
                 -4: "PPR_ERR_NOT_CONVERGED", -5: "PPR_ERR_CUDA", -6: "PPR_ERR_ADMIT"}

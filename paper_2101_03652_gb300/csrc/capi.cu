@@ -42,6 +42,10 @@ ppr_status ppr_sssp_query(ppr_graph* g, const int32_t* src, int32_t k, ppr_mode 
     }
     if (o.epoch_num < 0 || o.epoch_num > 64) { set_error("epoch_num must lie in [0, 64]"); return PPR_ERR_ARG; }
     if (o.epoch_num > 0 && o.warm_start) { set_error("epoch_num and warm_start exclude each other"); return PPR_ERR_ARG; }
+    if ((o.flags & PPR_FLAG_NO_ACTIVE) && o.epoch_num == 0) {
+      set_error("PPR_FLAG_NO_ACTIVE needs the residue form: set epoch_num > 0");
+      return PPR_ERR_ARG;
+    }
     if (out_walk_counts) { set_error("walk counts exist only in APPROX mode"); return PPR_ERR_ARG; }
   } else if (mode == PPR_APPROX) {
     if (!(o.eps > 0.0) || !std::isfinite(o.eps)) { set_error("eps must be > 0"); return PPR_ERR_ARG; }

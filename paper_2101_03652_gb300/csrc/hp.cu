@@ -339,8 +339,8 @@ static void launch_sweep(const SweepArgs& a, int grid, cudaStream_t st) {
 // residue sum is at most lambda^(i/E) or no node is active.
 template <int KT>
 static ppr_status run_epochs(ppr_graph* g, const ppr_graph::SweepPlan& plan, int grid, int grid_ew, int E,
-                             double lambda, double alpha, int max_sweeps, int ncols, u64* r, u64* pi, u64* ya,
-                             u64* yb, u64* ctr, u64* hpin, int& sweeps, std::vector<double>& rsum,
+                             bool until_inactive, double lambda, double alpha, int max_sweeps, int ncols, u64* r,
+                             u64* pi, u64* ya, u64* yb, u64* ctr, u64* hpin, int& sweeps, std::vector<double>& rsum,
                              int64_t& launches, float& ms_sweep, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st) {
   const int64_t n = g->n, m = g->m;
   EpochArgs ea;
@@ -363,10 +363,13 @@ static ppr_status run_epochs(ppr_graph* g, const ppr_graph::SweepPlan& plan, int
     for (int c = 0; c < ncols; ++c) mx = std::max(mx, rsum[c]);
     return mx;
   };
-  for (int i = 1; i <= E; ++i) {
-    const double thr = std::pow(lambda, (double)i / (double)E);  // m r'_max
+  // epochs 1..E; with until_inactive one more round at r_max = lambda/m that
+  // ends only when no node is active (it cannot end on the residue sum)
+  for (int i = 1; i <= E + (until_inactive ? 1 : 0); ++i) {
+    const bool last = i > E;
+    const double thr = std::pow(lambda, (double)std::min(i, E) / (double)E);  // m r'_max
     const u64 rmax_raw = (u64)std::max(1.0, std::floor(thr / (double)m * kFixOne));
-    if (max_rsum() <= thr) continue;
+    if (!last && max_rsum() <= thr) continue;
     PPR_CUDA_TRY(cudaMemsetAsync(ctr + 64, 0, 8, st));
     epoch_activate_kernel<KT><<<grid_ew, 256, 0, st>>>(n, g->d_deg, g->d_omega, r, rmax_raw, ya, ctr + 64);
     ++launches;
@@ -399,7 +402,7 @@ static ppr_status run_epochs(ppr_graph* g, const ppr_graph::SweepPlan& plan, int
         rsum[c] = (double)hpin[c] / kFixOne;
         act += hpin[64 + c];
       }
-      if (max_rsum() <= thr || act == 0) break;
+      if ((!last && max_rsum() <= thr) || act == 0) break;
     }
   }
   return PPR_OK;
@@ -710,12 +713,14 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
     std::vector<int64_t> pushed(KT, 0);
     int levels = 0;
     bool all_done = false;
+    bool frontier_empty = false;  // the queue phase ended with no active node
     bool have_state = false;  // (r, pi) hold a push state
     // a learned estimate either replaces the zero start (correction_passes = 0)
     // or corrects the remaining mass after `corr` passes of the zero-start solve
     const int corr = o.warm_start ? warm_correction_passes(o.warm_start) : 0;
     const bool warm = o.warm_start != nullptr && corr == 0;
     const bool partial = (o.flags & PPR_FLAG_PARTIAL) != 0;
+    const bool no_active = (o.flags & PPR_FLAG_NO_ACTIVE) != 0;
     const bool refine = !partial && (o.flags & (PPR_FLAG_SYNC | PPR_FLAG_FIXED_PASSES)) == 0;
     bool corrected = false;
     if (switch_edges != 0 && !warm) {
@@ -767,7 +772,8 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
           pushed[c] = (int64_t)hpin[3 + KT + c];
           if (rraw > lambda_raw) all_done = false;
         }
-        if (all_done || nfront == 0) break;
+        frontier_empty = nfront == 0;
+        if ((all_done && !no_active) || nfront == 0) break;
         if ((int64_t)fedges > switch_edges) break;
         if (levels > max_sweeps) { set_error("queue phase did not finish"); status = PPR_ERR_NOT_CONVERGED; break; }
         std::swap(fa, fb);
@@ -781,7 +787,8 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
     int sweeps = 0, fp32_passes = 0, refine_cycles = 0;
     std::vector<double> bound(KT, 0.0);
     u64* xfinal = pi;  // the estimate to output
-    bool need_dense = !all_done;
+    // the no-active end state also needs the frontier emptied
+    bool need_dense = !all_done || (no_active && !frontier_empty);
     if (!need_dense) {
       for (int c = 0; c < ncols; ++c) bound[c] = rsum[c];
     } else if (o.epoch_num > 0) {
@@ -796,8 +803,8 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
         for (int c = 0; c < ncols; ++c) rsum[c] = 1.0;
       }
       for (int c = 0; c < ncols; ++c) r0[c] = rsum[c];
-      status = run_epochs<KT>(g, plan, sweep_grid, grid_ew, o.epoch_num, lambda, alpha, max_sweeps, ncols, r, pi, za,
-                              zb, counters + 1024, hpin, sweeps, rsum, launches, ms_sweep, es0, es1, st);
+      status = run_epochs<KT>(g, plan, sweep_grid, grid_ew, o.epoch_num, no_active, lambda, alpha, max_sweeps, ncols,
+                              r, pi, za, zb, counters + 1024, hpin, sweeps, rsum, launches, ms_sweep, es0, es1, st);
       if (status != PPR_OK) break;
       sweep_launches += sweeps;
       // each pass rounds d shares per node by at most half a unit each

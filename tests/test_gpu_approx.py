@@ -101,3 +101,28 @@ def test_rmat22_configuration_sampled(P):
         assert abs(pi[i].sum() - 1.0) < 1e-4
     oc, _, ost = O.walks(og, r[0], st[0]["W"], SEED, 0, ALPHA)
     assert np.array_equal(counts[0], oc)
+
+
+def test_eps_sweep_accuracy(P):
+    """The accuracy study over eps on a small graph: the relative-error
+    guarantee holds at every eps (entries with pi >= 1/n, against an exact
+    vector), with walks and with the index, and the l1 error falls as eps
+    does."""
+    rp, ci = gen.chung_lu(3000, 30000, 2.2, seed=5)
+    og = O.Graph(rp, ci)
+    n = og.n
+    src = gen.sources(n, 4, seed=11)
+    exact = np.stack([O.powitr(og, int(s), ALPHA, 1e-13)[0] for s in src])
+    g = P.Graph(rp, ci)
+    g.build_index(0x1DE5, ALPHA)
+    l1 = {}
+    for eps in (0.1, 0.3, 0.5):
+        for flags in (0, P.PPR_FLAG_INDEX):
+            pi, _ = g.query(np.asarray(src, dtype=np.int32), P.PPR_APPROX, eps=eps, seed=SEED, flags=flags)
+            pi = pi.cpu().numpy()
+            big = exact >= 1.0 / n
+            assert np.all(np.abs(pi - exact)[big] <= eps * exact[big]), (eps, flags)
+            l1[(eps, flags)] = np.abs(pi - exact).sum(axis=1).mean()
+    g.close()
+    for flags in (0, P.PPR_FLAG_INDEX):
+        assert l1[(0.1, flags)] < l1[(0.5, flags)]

@@ -269,3 +269,54 @@ def test_fp32_refinement_residual_output(P, c0, c0_ref):
         ref_r = O.residual(og, int(s), out[i], ALPHA)
         assert np.abs(out_r[i] - ref_r).sum() <= 1e-12 + 1e-6 * np.abs(ref_r).sum()
         assert np.abs(out_r[i]).sum() <= st[i]["final_l1_residual"]
+
+
+def _no_active_query(P, rp, ci, src, **kw):
+    n = len(rp) - 1
+    g = P.Graph(rp, ci)
+    out_r = torch.empty((len(src), n), dtype=torch.float64, device="cuda")
+    pi, st = g.query(src, P.PPR_HP, out_r=out_r, lam=LAM, epoch_num=8, flags=P.PPR_FLAG_NO_ACTIVE, **kw)
+    torch.cuda.synchronize()
+    res = pi.cpu().numpy(), out_r.cpu().numpy(), st
+    g.close()
+    return res
+
+
+def test_no_active_end_state(P, c0, c0_ref):
+    """PPR_FLAG_NO_ACTIVE with epochs: the Remark after Algorithm 3 -- the
+    returned residue has no active node w.r.t. lambda/m, the answer is still
+    within 2 lambda of the oracle and the residue sum certifies it."""
+    rp, ci, src = c0
+    m = len(ci)
+    d = np.diff(rp)
+    pi, r, st = _no_active_query(P, rp, ci, src[:4])
+    for i, s in enumerate(src[:4]):
+        assert np.abs(pi[i] - c0_ref[int(s)]).sum() <= 2 * LAM
+        assert r[i].min() >= 0.0
+        assert np.all(r[i] <= d * (LAM / m))          # no active node
+        assert r[i].sum() <= st[i]["final_l1_residual"] + 1e-15
+    with pytest.raises(P.PPRError):                   # needs the residue form
+        g = P.Graph(rp, ci)
+        try:
+            g.query(src[:1], P.PPR_HP, lam=LAM, flags=P.PPR_FLAG_NO_ACTIVE)
+        finally:
+            g.close()
+
+
+def test_fifo_only_gpu_mode(P, c0, c0_ref):
+    """A switch threshold no level reaches keeps the whole query in the queue
+    phase: FIFO-FwdPush (Algorithm 2) by levels, run to no active node.  Edge
+    pushes are compared with the sequential oracle's (same level structure,
+    different order inside a level)."""
+    rp, ci, src = c0
+    m = len(ci)
+    d = np.diff(rp)
+    og = O.Graph(rp, ci)
+    pi, r, st = _no_active_query(P, rp, ci, src[:3], switch_edges=1 << 62, k_tile=1)
+    for i, s in enumerate(src[:3]):
+        assert st[i]["sweeps"] == 0 and st[i]["levels"] > 0
+        assert np.abs(pi[i] - c0_ref[int(s)]).sum() <= 2 * LAM
+        assert np.all(r[i] <= d * (LAM / m))
+        _, _, ost = O.fifo_fwdpush(og, int(s), ALPHA, lam=LAM)
+        ratio = st[i]["edges_pushed"] / ost["edge_pushes"]
+        assert 0.5 <= ratio <= 2.0, ratio
