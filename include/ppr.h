@@ -54,8 +54,9 @@ typedef enum {
                               passes at lambda/m continue until no node is active.  With a
                               switch_edges that no level reaches, the call is FIFO-FwdPush
                               (Algorithm 2) by levels on the GPU */
+#define PPR_FLAG_FP32_ONLY 32 /* HP: correction passes with FP32 z_e only (no BF16 stage) */
 #define PPR_FLAG_FIXED_PASSES 8 /* HP: every pass in Q1.63.  By default the dense phase
-                              solves for the remaining error e = pi - X with FP32 passes,
+                              solves for the remaining error e = pi - X with BF16 and FP32 passes,
                               folds e into the Q1.63 estimate X and certifies with one
                               exact synchronous Q1.63 pass (iterative refinement); the
                               bound and its guarantee are the same either way */
@@ -104,9 +105,13 @@ typedef struct {
   int64_t kernel_launches;      /* kernels this call launched */
   int64_t sweep_launches;       /* of which sweep-kernel launches */
   double W;                     /* APPROX: walk budget of Eq. 8 (natural log) */
-  int32_t fp32_passes;          /* HP: of `sweeps`, FP32 correction passes (the rest are Q1.63) */
+  int32_t fp32_passes;          /* HP: of `sweeps`, correction passes with FP32 z_e */
   int32_t refine_cycles;        /* HP: fold + exact-pass cycles of the refinement */
-  double ms_fp32;               /* HP: device time of the FP32 passes (part of ms_sweep) */
+  double ms_fp32;               /* HP: device time of the FP32 correction passes (part of ms_sweep) */
+  int32_t bf16_passes;          /* HP: of `sweeps`, correction passes with BF16 z_e (the rest
+                                   of `sweeps` are Q1.63) */
+  int32_t reserved;
+  double ms_bf16;               /* HP: device time of the BF16 correction passes (part of ms_sweep) */
 } ppr_stats;
 
 /* Fill opts with defaults: alpha 0.2, lambda 1e-8, eps 0.5, mu 0 (=1/n),

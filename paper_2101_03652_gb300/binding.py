@@ -22,6 +22,7 @@ PPR_FLAG_SYNC = 2
 PPR_FLAG_INDEX = 4
 PPR_FLAG_FIXED_PASSES = 8
 PPR_FLAG_NO_ACTIVE = 16
+PPR_FLAG_FP32_ONLY = 32
 
 STATUS_NAMES = {0: "PPR_OK", -1: "PPR_ERR_ARG", -2: "PPR_ERR_GRAPH", -3: "PPR_ERR_OOM",
                 -4: "PPR_ERR_NOT_CONVERGED", -5: "PPR_ERR_CUDA", -6: "PPR_ERR_ADMIT"}
@@ -70,6 +71,9 @@ class ppr_stats(ctypes.Structure):
         ("fp32_passes", ctypes.c_int32),
         ("refine_cycles", ctypes.c_int32),
         ("ms_fp32", ctypes.c_double),
+        ("bf16_passes", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("ms_bf16", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -422,19 +422,37 @@ struct RefineTile {
   int corr = 0;
   const int32_t* src_new = nullptr;
   u64* mass = nullptr;       // [KT] device scratch for exact column sums
+  bool fp32_only = false;    // no BF16 stage
 };
 
-// Sweep phase with FP32 correction passes (see refine_kernel.cuh).  Buffers:
-// pi = X (Q1.63 base); r = the push residue, then e of the FP32 passes, then
-// X' of the exact pass; zb = [r_f | z_e]; za = the second z_e buffer, then
-// z(X) for the exact pass.  Every stop is certified by an exact synchronous
-// pass: ||pi - X'||_1 <= (1-alpha) ||X' - X||_1 / alpha.  The answer is X' (r).
+// Sweep phase with correction passes (see refine_kernel.cuh).  Buffers:
+// pi = X (Q1.63 base); r = the push residue, then e of the correction passes,
+// then X' of the exact pass; zb = [r_f f32 | z_e]; za = the second z_e buffer,
+// then z(X) for the exact pass.  Each cycle runs BF16 passes while they
+// contract (down to about 1e-2 of the cycle's start), then FP32 passes (down
+// to about 1e-6), folds e into X and runs one exact synchronous pass, which
+// certifies the stop: ||pi - X'||_1 <= (1-alpha) ||X' - X||_1 / alpha.  The
+// answer is X' (in r).
+struct RefineOut {
+  int passes[2] = {0, 0};    // BF16, FP32 correction passes
+  float ms[2] = {0.f, 0.f};  // their device time
+  int cycles = 0;
+};
+
+template <int KT, typename T>
+static ppr_status refine_kernel_setup(ppr_graph* g, Plan** plan, int* grid, cudaStream_t st) {
+  PPR_TRY(get_plan(g, RLay<KT, T>::L, plan, st));
+  int bps = 0;
+  PPR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, refine_pass_kernel<KT, T>, 256, 0));
+  *grid = sm_count() * std::max(bps, 1);
+  return PPR_OK;
+}
+
 template <int KT>
 static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int grid_ew, SweepArgs sa,
                              const RefineTile& t, double* resid, u64* hpin, int& sweeps, int64_t& launches,
-                             std::vector<double>& bound, std::vector<double>& r0, float& ms_sweep,
-                             int& fp32_passes, int& cycles, float& ms_fp32, cudaEvent_t es0, cudaEvent_t es1,
-                             cudaStream_t st) {
+                             std::vector<double>& bound, std::vector<double>& r0, float& ms_sweep, RefineOut& ro,
+                             cudaEvent_t es0, cudaEvent_t es1, cudaStream_t st) {
   const int64_t n = g->n, m = g->m;
   const size_t cells = (size_t)n * KT;
   const int ncols = t.ncols;
@@ -444,30 +462,43 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
   u64* Xn = ws.r.as<u64>();
   u64* za = ws.za.as<u64>();
   float* rf = ws.zb.as<float>();
-  float* ze_a = rf + cells;
-  float* ze_b = ws.za.as<float>();
+  void* zbuf_a = rf + cells;  // 4 cells bytes each: one FP32 or one BF16 z_e array
+  void* zbuf_b = ws.za.ptr;
   float* ef = ws.r.as<float>();
   const float oma = (float)(1.0 - alpha);
 
-  Plan* fplan = nullptr;
-  PPR_TRY(get_plan(g, Lay32<KT>::L, &fplan, st));
-  int bps = 0;
-  PPR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, refine_pass_kernel<KT>, 256, 0));
-  const int fgrid = sm_count() * std::max(bps, 1);
+  Plan* plans[2] = {nullptr, nullptr};
+  int grids[2] = {0, 0};
+  PPR_TRY((refine_kernel_setup<KT, bf16>(g, &plans[0], &grids[0], st)));
+  PPR_TRY((refine_kernel_setup<KT, float>(g, &plans[1], &grids[1], st)));
   RefArgs ra;
-  ra.items = fplan->d_items;
   ra.in_rp = g->d_in_rp;
   ra.in_ci = g->d_in_ci;
   ra.deg = g->d_deg;
   ra.rf = rf;
   ra.one_minus_alpha = oma;
-  ra.npieces = fplan->d_npieces;
   ra.heavy_acc = ws.heavy_acc.as<float>();
   ra.heavy_cnt = ws.heavy_cnt.as<unsigned int>();
+  const bool use_bf16 = !t.fp32_only;
+
+  const double slack = (double)m * 0.5 / kFixOne / alpha;
+  // goal of the correction passes: after the fold the exact pass measures
+  // ||X' - X||_1 of about (1-alpha) F (F = the last measured ||e' - e||_1), so
+  // the certified bound comes out near (1-alpha)^2 F / alpha; aim at 0.6 lambda
+  const double target_f = 0.6 * lambda * alpha / ((1.0 - alpha) * (1.0 - alpha));
+  const double floor_rel[2] = {1e-2, 1e-6};  // where BF16 / FP32 passes stop contracting
+  // the cycle's goal and the precision it starts in (0 = BF16 z_e, 1 = FP32):
+  // BF16 only for a cycle whose whole reduction fits above its floor (about
+  // 1e-2 of the start; typically the last cycle); where more is needed BF16
+  // passes contract worse and leave the work to FP32.  The setup kernels
+  // write z_e in the precision chosen here.
+  auto cycle_goal = [&](double f0) { return std::max(target_f, floor_rel[1] * f0); };
+  auto cycle_prec = [&](double f0) { return (use_bf16 && cycle_goal(f0) >= 2.0 * floor_rel[0] * f0) ? 0 : 1; };
 
   double F0 = 0.0;  // ||r||_1 of the cycle = ||e_1 - e_0||_1
   const bool warm_x0 = t.model && t.corr == 0;
   bool corr_pending = t.model && t.corr > 0;
+  int prec0 = 1;
   if (warm_x0) {
     // X = the model's estimate; the first exact pass measures its residual
     PPR_TRY(warm_start_tile(t.model, g, t.src_new, ncols, KT, alpha, za, X, st));
@@ -475,35 +506,51 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
   } else {
     // cycle 0: X = reserve, r = alpha r_push
     for (int c = 0; c < ncols; ++c) F0 = std::max(F0, alpha * (t.have_state ? t.rsum[c] : 1.0));
-    refine_setup_push_kernel<KT><<<grid_ew, 256, 0, st>>>(n, Xn, alpha, g->d_deg, oma, rf, ze_a);
+    prec0 = corr_pending ? 1 : cycle_prec(F0);  // the correction model follows FP32 passes
+    if (prec0 == 0)
+      refine_setup_push_kernel<KT, bf16><<<grid_ew, 256, 0, st>>>(n, Xn, alpha, g->d_deg, oma, rf,
+                                                                  static_cast<bf16*>(zbuf_a));
+    else
+      refine_setup_push_kernel<KT, float><<<grid_ew, 256, 0, st>>>(n, Xn, alpha, g->d_deg, oma, rf,
+                                                                   static_cast<float*>(zbuf_a));
     ++launches;
   }
-  const double slack = (double)m * 0.5 / kFixOne / alpha;
-  // FP32 goal: after the fold the exact pass measures ||X' - X||_1 of about
-  // (1-alpha) F (F = the last measured ||e' - e||_1), so the certified bound
-  // comes out near (1-alpha)^2 F / alpha; aim at 0.6 lambda
-  const double target_f = 0.6 * lambda * alpha / ((1.0 - alpha) * (1.0 - alpha));
-  double rate = -1.0;  // observed contraction per FP32 pass
+  double rate = -1.0;  // observed contraction per pass
   for (int cycle = 0;; ++cycle) {
     if (cycle >= 8) {
       set_error("refinement did not certify within 8 cycles");
       return PPR_ERR_NOT_CONVERGED;
     }
-    // ---- FP32 passes: in place, the last of each batch synchronous, measured,
-    // and writing e for the fold
-    const double goal = std::max(target_f, 1e-6 * F0);  // FP32 sums stop contracting near 1e-6 F0
+    // ---- correction passes: in place, the last of each batch synchronous,
+    // measured, and writing e for the fold
+    const double goal = cycle_goal(F0);
+    int prec = prec0;  // the precision the setup wrote z_e in
     double F = F0;
-    float* zcur = ze_a;
-    float* znext = ze_b;
+    void* zcur = zbuf_a;
+    void* znext = zbuf_b;
+    bool ran = false;
     while (!(warm_x0 && cycle == 0) && F > goal) {
+      const double phase_goal = std::max(goal, floor_rel[prec] * F0);
+      if (F <= phase_goal && prec == 0) {
+        // BF16 done: continue in FP32 from the same e (z_e widened exactly)
+        bf16_to_f32_kernel<<<grid_ew, 256, 0, st>>>((int64_t)cells, static_cast<const bf16*>(zcur),
+                                                      static_cast<float*>(znext));
+        ++launches;
+        std::swap(zcur, znext);
+        prec = 1;
+        continue;
+      }
       const double cr = rate > 0.0 ? rate : (1.0 - alpha);
-      int S = std::max((int)std::ceil(std::log(goal / F) / std::log(cr) - 1e-12), 1);
+      int S = std::max((int)std::ceil(std::log(phase_goal / F) / std::log(cr) - 1e-12), 1);
       if (rate <= 0.0) S = std::min(S, 16);  // learn the rate first
       if (corr_pending) S = t.corr;          // the passes the correction model was trained after
       if (sweeps + S + 1 > t.max_sweeps) {
         set_error("sweep limit %d reached", t.max_sweeps);
         return PPR_ERR_NOT_CONVERGED;
       }
+      const Plan* fp = plans[prec];
+      ra.items = fp->d_items;
+      ra.npieces = fp->d_npieces;
       PPR_CUDA_TRY(cudaMemsetAsync(resid, 0, 64 * 8, st));
       PPR_CUDA_TRY(cudaEventRecord(es0, st));
       for (int j = 0; j < S; ++j) {
@@ -514,36 +561,54 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
         ra.resid = last ? resid : nullptr;
         // rows without in-edges keep z_e = r_f (1-alpha)/d from the setup; the
         // synchronous pass rewrites every row of the other buffer
-        ra.n_items = last ? fplan->n_items_all : fplan->n_items_nz;
-        refine_pass_kernel<KT><<<fgrid, 256, 0, st>>>(ra);
+        ra.n_items = last ? fp->n_items_all : fp->n_items_nz;
+        if (prec == 0)
+          refine_pass_kernel<KT, bf16><<<grids[0], 256, 0, st>>>(ra);
+        else
+          refine_pass_kernel<KT, float><<<grids[1], 256, 0, st>>>(ra);
       }
       PPR_CUDA_TRY(cudaEventRecord(es1, st));
       PPR_CUDA_TRY(cudaGetLastError());
       std::swap(zcur, znext);
+      ran = true;
       sweeps += S;
-      fp32_passes += S;
+      ro.passes[prec] += S;
       launches += S;
       PPR_CUDA_TRY(cudaMemcpyAsync(hpin, resid, 64 * 8, cudaMemcpyDeviceToHost, st));
       PPR_CUDA_TRY(cudaStreamSynchronize(st));
       float a_ms = 0.f;
       cudaEventElapsedTime(&a_ms, es0, es1);
       ms_sweep += a_ms;
-      ms_fp32 += a_ms;
+      ro.ms[prec] += a_ms;
       const double* D = reinterpret_cast<const double*>(hpin);
       double Fm = 0.0;
       for (int c = 0; c < ncols; ++c) Fm = std::max(Fm, D[c]);
       if (!(Fm >= 0.0) || !std::isfinite(Fm)) {
-        set_error("FP32 correction passes diverged");
+        set_error("correction passes diverged");
         return PPR_ERR_NOT_CONVERGED;
       }
-      if (Fm > 0.0 && Fm < F && S >= 2)
+      // stalled: the batch achieved less than a quarter of the log-reduction
+      // that (1-alpha) per pass guarantees in exact arithmetic (any batch
+      // length): the precision's floor is reached
+      const bool stalled = Fm > F * std::pow(1.0 - alpha, 0.25 * S);
+      if (Fm > 0.0 && Fm < F && S >= 2 && !stalled)
         rate = std::min(1.0 - alpha, std::max(0.05, std::pow(Fm / F, 1.0 / S)));
-      const bool stalled = S >= 3 && Fm > 0.7 * F;
       F = Fm;
-      if (stalled || corr_pending) break;
+      if (corr_pending) break;
+      if (stalled) {
+        if (prec == 1) break;
+        if (F > goal) {
+          // BF16 stopped contracting: continue in FP32 from the same e
+          bf16_to_f32_kernel<<<grid_ew, 256, 0, st>>>((int64_t)cells, static_cast<const bf16*>(zcur),
+                                                        static_cast<float*>(znext));
+          ++launches;
+          std::swap(zcur, znext);
+          prec = 1;
+        }
+      }
     }
     if (!(warm_x0 && cycle == 0)) {
-      if (F == F0) {
+      if (!ran) {
         // nothing ran (r already below the goal): e = r
         PPR_CUDA_TRY(cudaMemcpyAsync(ef, rf, cells * 4, cudaMemcpyDeviceToDevice, st));
       }
@@ -574,7 +639,7 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
     PPR_CUDA_TRY(cudaGetLastError());
     ++sweeps;
     ++launches;
-    ++cycles;
+    ++ro.cycles;
     PPR_CUDA_TRY(cudaMemcpyAsync(hpin, resid, 64 * 8, cudaMemcpyDeviceToHost, st));
     PPR_CUDA_TRY(cudaStreamSynchronize(st));
     {
@@ -593,8 +658,14 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
       if (warm_x0 && cycle == 0) r0[c] = Dc;  // measured ||r(x0)||_1 of the model's estimate
     }
     if (ok) return PPR_OK;
-    // next cycle from X: r = X' - X
-    refine_setup_resid_kernel<KT><<<grid_ew, 256, 0, st>>>(n, Xn, X, g->d_deg, oma, rf, ze_a);
+    // next cycle from X: r = X' - X, z_e in the precision the cycle starts in
+    prec0 = cycle_prec(F0);
+    if (prec0 == 0)
+      refine_setup_resid_kernel<KT, bf16><<<grid_ew, 256, 0, st>>>(n, Xn, X, g->d_deg, oma, rf,
+                                                                   static_cast<bf16*>(zbuf_a));
+    else
+      refine_setup_resid_kernel<KT, float><<<grid_ew, 256, 0, st>>>(n, Xn, X, g->d_deg, oma, rf,
+                                                                    static_cast<float*>(zbuf_a));
     ++launches;
   }
 }
@@ -697,7 +768,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
   PPR_CUDA_TRY(cudaEventCreate(&ev2));
   PPR_CUDA_TRY(cudaEventCreate(&es0));
   PPR_CUDA_TRY(cudaEventCreate(&es1));
-  float ms_push = 0.f, ms_sweep = 0.f, ms_total = 0.f, ms_fp32 = 0.f;
+  float ms_push = 0.f, ms_sweep = 0.f, ms_total = 0.f, ms_fp32 = 0.f, ms_bf16 = 0.f;
   int64_t launches = 0, sweep_launches = 0;
 
   ppr_status status = PPR_OK;
@@ -784,7 +855,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
     PPR_CUDA_TRY(cudaEventRecord(ev1, st));
 
     // ---- sweep phase
-    int sweeps = 0, fp32_passes = 0, refine_cycles = 0;
+    int sweeps = 0, fp32_passes = 0, bf16_passes = 0, refine_cycles = 0;
     std::vector<double> bound(KT, 0.0);
     u64* xfinal = pi;  // the estimate to output
     // the no-active end state also needs the frontier emptied
@@ -846,8 +917,15 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
       rt.corr = corr;
       rt.src_new = src_new;
       rt.mass = mass;
+      rt.fp32_only = (o.flags & PPR_FLAG_FP32_ONLY) != 0;
+      RefineOut ro;
       status = run_refine<KT>(g, plan, sweep_grid, grid_ew, sa, rt, resid, hpin, sweeps, launches, bound, r0,
-                              ms_sweep, fp32_passes, refine_cycles, ms_fp32, es0, es1, st);
+                              ms_sweep, ro, es0, es1, st);
+      bf16_passes = ro.passes[0];
+      fp32_passes = ro.passes[1];
+      refine_cycles = ro.cycles;
+      ms_bf16 += ro.ms[0];
+      ms_fp32 += ro.ms[1];
       if (status != PPR_OK) break;
       sweep_launches += sweeps;
       xfinal = r;
@@ -1022,6 +1100,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
         s.final_l1_residual = bound[c];
         s.mass_deficit = 1.0 - (double)hpin[c] / kFixOne;
         s.fp32_passes = fp32_passes;
+        s.bf16_passes = bf16_passes;
         s.refine_cycles = refine_cycles;
       }
     }
@@ -1039,6 +1118,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
       stats[i].ms_sweep = ms_sweep;
       stats[i].ms_total = ms_total;
       stats[i].ms_fp32 = ms_fp32;
+      stats[i].ms_bf16 = ms_bf16;
       stats[i].kernel_launches = launches;
       stats[i].sweep_launches = sweep_launches;
     }

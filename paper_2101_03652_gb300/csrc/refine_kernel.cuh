@@ -1,29 +1,38 @@
-// FP32 correction passes of the high-precision path (mixed-precision
-// iterative refinement around the exact Q1.63 passes).
+// Correction passes of the high-precision path (mixed-precision iterative
+// refinement around the exact Q1.63 passes).
 //
 // For a base estimate X (Q1.63) the remaining error e = pi - X solves
 // e = r + (1-alpha) e P, the same contraction as Eq. 7 with r in place of
 // alpha e_s: r = alpha r_push when X is the reserve of a push state (then
 // pi = X + sum_v r_push(v) pi_v), r = X' - X when X' is one exact pass from X.
-// These passes solve it in FP32 (half the bytes of a Q1.63 gather), the result
-// is folded into X, and an exact pass measures ||X' - X||_1, which certifies
-// the stop exactly as before: the precision of the FP32 passes decides how
-// fast the bound falls, never whether it holds.
+// These passes solve it with FP32 arithmetic, the gathered z_e = (1-alpha) e/d
+// stored in FP32 (half the bytes of a Q1.63 gather) or BF16 (a quarter; its
+// rounding stalls the iteration near 1e-2 of the cycle's start, so it serves
+// the first part of a cycle).  The result is folded into X, and an exact pass
+// measures ||X' - X||_1, which certifies the stop exactly as before: the
+// precision of these passes decides how fast the bound falls, never whether
+// it holds.
 #pragma once
+
+#include <cuda_bf16.h>
+
+#include <type_traits>
 
 #include "f32_lanes.cuh"
 #include "sweep_kernel.cuh"
 
 namespace ppr {
 
+typedef __nv_bfloat16 bf16;
+
 struct RefArgs {
   int32_t n_items;
-  const int4* items;  // work list for Lay32<KT>::L lanes per row
+  const int4* items;  // work list for RLay<KT, T>::L lanes per row
   const int32_t* in_rp;
   const int32_t* in_ci;
   const int32_t* deg;
-  const float* ze_in;  // (1-alpha) e / d
-  float* ze_out;
+  const void* ze_in;   // (1-alpha) e / d, FP32 or BF16 [n][KT]
+  void* ze_out;        // same type as ze_in
   const float* rf;     // r of the cycle
   float* e_out;        // e of this pass (NULL: not written)
   float one_minus_alpha;
@@ -33,17 +42,102 @@ struct RefArgs {
   double* resid;       // [KT] sums of |e_new - e_old| (NULL: not measured)
 };
 
-// gathers in flight per lane and blocks per SM: wide tiles keep more gathers
-// per warp; narrow ones more warps (measured on R-MAT scale 20)
-template <int KT>
-struct RefTune {
-  static constexpr int UNR = KT >= 32 ? 8 : 4;
-  static constexpr int MIN_BLOCKS = KT >= 32 ? 6 : 8;
+// a lane loads 16 B of a node's tile row (V values of T); L lanes cover the row
+template <int KT, typename T>
+struct RLay {
+  static constexpr int VMAX = 16 / (int)sizeof(T);
+  static constexpr int V = KT < VMAX ? KT : VMAX;
+  static constexpr int L = KT / V;
+  static constexpr int EPW = 32 / L;
 };
 
+// gathers in flight per lane and blocks per SM (measured on R-MAT scale 20):
+// FP32 rows: wide rows keep more gathers per warp, narrow ones more warps;
+// BF16 rows carry 8 columns per lane, whose sums need 64 registers
+template <int KT, typename T>
+struct RefTune {
+  static constexpr bool kBf16 = sizeof(T) == 2;
+  static constexpr int UNR = kBf16 ? 8 : (RLay<KT, T>::L >= 8 ? 8 : 4);
+  static constexpr int MIN_BLOCKS = kBf16 ? 4 : (RLay<KT, T>::L >= 8 ? 6 : 8);
+};
+
+// raw 16-byte (or narrower) row piece of V values of T, converted to FP32 when summed
+template <typename T, int V>
+struct Raw;
+template <>
+struct Raw<float, 4> { typedef float4 type; };
+template <>
+struct Raw<float, 2> { typedef float2 type; };
+template <>
+struct Raw<float, 1> { typedef float type; };
+template <>
+struct Raw<bf16, 8> { typedef uint4 type; };
+template <>
+struct Raw<bf16, 4> { typedef uint2 type; };
+template <>
+struct Raw<bf16, 2> { typedef unsigned int type; };
+template <>
+struct Raw<bf16, 1> { typedef unsigned short type; };
+
+template <typename T, int V>
+__device__ __forceinline__ typename Raw<T, V>::type ld_raw(const T* p) {
+  return __ldg(reinterpret_cast<const typename Raw<T, V>::type*>(p));
+}
+template <typename T, int V>
+__device__ __forceinline__ typename Raw<T, V>::type zero_raw() {
+  typename Raw<T, V>::type z{};
+  return z;
+}
+
+// BF16 -> FP32 is exact: the 16 stored bits are the high half of the float
+__device__ __forceinline__ float bf_lo(unsigned w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
+
+template <typename T, int V>
+__device__ __forceinline__ void add_raw(float (&acc)[V], const typename Raw<T, V>::type& t) {
+  if constexpr (std::is_same<T, float>::value) {
+    if constexpr (V == 4) { acc[0] += t.x; acc[1] += t.y; acc[2] += t.z; acc[3] += t.w; }
+    else if constexpr (V == 2) { acc[0] += t.x; acc[1] += t.y; }
+    else { acc[0] += t; }
+  } else {
+    if constexpr (V == 8) {
+      acc[0] += bf_lo(t.x); acc[1] += bf_hi(t.x); acc[2] += bf_lo(t.y); acc[3] += bf_hi(t.y);
+      acc[4] += bf_lo(t.z); acc[5] += bf_hi(t.z); acc[6] += bf_lo(t.w); acc[7] += bf_hi(t.w);
+    } else if constexpr (V == 4) {
+      acc[0] += bf_lo(t.x); acc[1] += bf_hi(t.x); acc[2] += bf_lo(t.y); acc[3] += bf_hi(t.y);
+    } else if constexpr (V == 2) {
+      acc[0] += bf_lo(t); acc[1] += bf_hi(t);
+    } else {
+      acc[0] += bf_lo((unsigned)t);
+    }
+  }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void ld_row(const T* p, float (&v)[V]) {
+#pragma unroll
+  for (int q = 0; q < V; ++q) v[q] = 0.f;
+  add_raw<T, V>(v, ld_raw<T, V>(p));
+}
+
+// FP32 row piece of V values (V up to 8)
 template <int V>
-__device__ __forceinline__ void stf(float* p, const float (&v)[V]) {
-  if constexpr (V == 4) {
+__device__ __forceinline__ void ld_f32(const float* p, float (&v)[V]) {
+  if constexpr (V == 8) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  } else {
+    ldf<V>(p, v);
+  }
+}
+
+template <int V>
+__device__ __forceinline__ void st_f32(float* p, const float (&v)[V]) {
+  if constexpr (V == 8) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+  } else if constexpr (V == 4) {
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
   } else if constexpr (V == 2) {
     *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
@@ -52,16 +146,71 @@ __device__ __forceinline__ void stf(float* p, const float (&v)[V]) {
   }
 }
 
+__device__ __forceinline__ unsigned pack_bf2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // .x = a (low half), .y = b
+  return *reinterpret_cast<const unsigned*>(&h);
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void st_row(T* p, const float (&v)[V]) {
+  if constexpr (std::is_same<T, float>::value) {
+    st_f32<V>(p, v);
+  } else if constexpr (V == 8) {
+    *reinterpret_cast<uint4*>(p) = make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]),
+                                              pack_bf2(v[6], v[7]));
+  } else if constexpr (V == 4) {
+    *reinterpret_cast<uint2*>(p) = make_uint2(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]));
+  } else if constexpr (V == 2) {
+    *reinterpret_cast<unsigned*>(p) = pack_bf2(v[0], v[1]);
+  } else {
+    *reinterpret_cast<bf16*>(p) = __float2bfloat16_rn(v[0]);
+  }
+}
+
+// row operands of the epilogue, r of the row (read-only for the whole pass)
+// and d.  BF16 passes load them before the row's gathers so that their
+// latency overlaps them; FP32 passes, short of registers, load them after
+// (measured both ways on R-MAT scale 20: each choice is the faster one)
+template <int V>
+struct RowPre {
+  float r[V];
+  float d;
+};
+
+template <typename T>
+constexpr bool kPrefetchRow = sizeof(T) == 2;
+
+template <int KT, typename T>
+__device__ __forceinline__ RowPre<RLay<KT, T>::V> refine_prefetch(const RefArgs& a, int u, int slot) {
+  constexpr int V = RLay<KT, T>::V;
+  RowPre<V> p;
+  if constexpr (kPrefetchRow<T>) {
+    ld_f32<V>(a.rf + (size_t)u * KT + slot * V, p.r);
+    p.d = (float)__ldg(&a.deg[u]);
+  }
+  return p;
+}
+
 // finish row u: e = r + sum, ze = e (1-alpha) / d
-template <int KT>
-__device__ __forceinline__ void refine_epilogue(const RefArgs& a, int u, int slot, const float (&acc)[Lay32<KT>::V],
-                                                float (&res)[Lay32<KT>::V]) {
-  constexpr int V = Lay32<KT>::V;
-  const float d = (float)__ldg(&a.deg[u]);
-  const float share = a.one_minus_alpha / d;
+template <int KT, typename T>
+__device__ __forceinline__ void refine_epilogue(const RefArgs& a, int u, int slot,
+                                                const RowPre<RLay<KT, T>::V>& pre,
+                                                const float (&acc)[RLay<KT, T>::V],
+                                                float (&res)[RLay<KT, T>::V]) {
+  constexpr int V = RLay<KT, T>::V;
   const size_t base = (size_t)u * KT + slot * V;
-  float r[V], e[V], zn[V];
-  ldf<V>(a.rf + base, r);  // read-only for the whole pass
+  float r[V];
+  float d;
+  if constexpr (kPrefetchRow<T>) {
+#pragma unroll
+    for (int q = 0; q < V; ++q) r[q] = pre.r[q];
+    d = pre.d;
+  } else {
+    ld_f32<V>(a.rf + base, r);
+    d = (float)__ldg(&a.deg[u]);
+  }
+  const float share = a.one_minus_alpha / d;
+  float e[V], zn[V];
 #pragma unroll
   for (int q = 0; q < V; ++q) {
     e[q] = r[q] + acc[q];
@@ -69,19 +218,20 @@ __device__ __forceinline__ void refine_epilogue(const RefArgs& a, int u, int slo
   }
   if (a.resid) {
     float zo[V];
-    ldf<V>(a.ze_in + base, zo);
+    ld_row<T, V>(static_cast<const T*>(a.ze_in) + base, zo);
     const float inv = d / a.one_minus_alpha;
 #pragma unroll
     for (int q = 0; q < V; ++q) res[q] += fabsf(zn[q] - zo[q]) * inv;
   }
-  stf<V>(a.ze_out + base, zn);
-  if (a.e_out) stf<V>(a.e_out + base, e);
+  st_row<T, V>(static_cast<T*>(a.ze_out) + base, zn);
+  if (a.e_out) st_f32<V>(a.e_out + base, e);
 }
 
-template <int KT>
+template <int KT, typename T>
 __device__ __forceinline__ void refine_gather_warp(const RefArgs& a, int e_begin, int e_end, int lane, int slot,
-                                                   float (&acc)[Lay32<KT>::V]) {
-  constexpr int V = Lay32<KT>::V, L = Lay32<KT>::L, EPW = Lay32<KT>::EPW, UNR = RefTune<KT>::UNR;
+                                                   float (&acc)[RLay<KT, T>::V]) {
+  constexpr int V = RLay<KT, T>::V, L = RLay<KT, T>::L, EPW = RLay<KT, T>::EPW, UNR = RefTune<KT, T>::UNR;
+  const T* z = static_cast<const T*>(a.ze_in);
   for (int base = e_begin; base < e_end; base += EPW * UNR) {
     int v[UNR];
 #pragma unroll
@@ -89,28 +239,21 @@ __device__ __forceinline__ void refine_gather_warp(const RefArgs& a, int e_begin
       const int e = base + q * EPW + lane / L;
       v[q] = e < e_end ? __ldg(&a.in_ci[e]) : -1;
     }
-    float t[UNR][V];
-#pragma unroll
-    for (int q = 0; q < UNR; ++q) {
-      if (v[q] >= 0) {
-        ldf<V>(a.ze_in + (size_t)v[q] * KT + slot * V, t[q]);
-      } else {
-#pragma unroll
-        for (int w = 0; w < V; ++w) t[q][w] = 0.f;
-      }
-    }
+    typename Raw<T, V>::type t[UNR];
 #pragma unroll
     for (int q = 0; q < UNR; ++q)
+      t[q] = v[q] >= 0 ? ld_raw<T, V>(z + (size_t)v[q] * KT + slot * V) : zero_raw<T, V>();
 #pragma unroll
-      for (int w = 0; w < V; ++w) acc[w] += t[q][w];
+    for (int q = 0; q < UNR; ++q) add_raw<T, V>(acc, t[q]);
   }
 }
 
-template <int KT>
-__global__ void __launch_bounds__(256, RefTune<KT>::MIN_BLOCKS) refine_pass_kernel(RefArgs a) {
-  constexpr int V = Lay32<KT>::V, L = Lay32<KT>::L;
+template <int KT, typename T>
+__global__ void __launch_bounds__(256, (RefTune<KT, T>::MIN_BLOCKS)) refine_pass_kernel(RefArgs a) {
+  constexpr int V = RLay<KT, T>::V, L = RLay<KT, T>::L;
   const int lane = threadIdx.x & 31;
   const int slot = lane % L;
+  const T* z = static_cast<const T*>(a.ze_in);
   float res[V];
 #pragma unroll
   for (int q = 0; q < V; ++q) res[q] = 0.f;
@@ -121,7 +264,7 @@ __global__ void __launch_bounds__(256, RefTune<KT>::MIN_BLOCKS) refine_pass_kern
       // piece of a split row; the last piece to arrive finishes the row
       const int u = w.y;
       float acc[V] = {};
-      refine_gather_warp<KT>(a, w.z, w.w, lane, slot, acc);
+      refine_gather_warp<KT, T>(a, w.z, w.w, lane, slot, acc);
 #pragma unroll
       for (int off = L; off < 32; off <<= 1)
 #pragma unroll
@@ -139,32 +282,30 @@ __global__ void __launch_bounds__(256, RefTune<KT>::MIN_BLOCKS) refine_pass_kern
           float tot[V];
 #pragma unroll
           for (int q = 0; q < V; ++q) tot[q] = atomicExch(&a.heavy_acc[(size_t)u * KT + slot * V + q], 0.f);
-          refine_epilogue<KT>(a, u, slot, tot, res);
+          refine_epilogue<KT, T>(a, u, slot, refine_prefetch<KT, T>(a, u, slot), tot, res);
         }
         if (lane == 0) atomicExch(&a.heavy_cnt[u], 0u);
       }
     } else if (w.x == 1) {
       for (int u = w.y; u < w.z; ++u) {
+        const auto pre = refine_prefetch<KT, T>(a, u, slot);
         float acc[V] = {};
-        refine_gather_warp<KT>(a, __ldg(&a.in_rp[u]), __ldg(&a.in_rp[u + 1]), lane, slot, acc);
+        refine_gather_warp<KT, T>(a, __ldg(&a.in_rp[u]), __ldg(&a.in_rp[u + 1]), lane, slot, acc);
 #pragma unroll
         for (int off = L; off < 32; off <<= 1)
 #pragma unroll
           for (int q = 0; q < V; ++q) acc[q] += __shfl_xor_sync(kFull, acc[q], off);
-        if (lane < L) refine_epilogue<KT>(a, u, slot, acc, res);
+        if (lane < L) refine_epilogue<KT, T>(a, u, slot, pre, acc, res);
       }
     } else {
       for (int u = w.y + lane / L; u < w.z; u += 32 / L) {
+        const auto pre = refine_prefetch<KT, T>(a, u, slot);
         const int e1 = __ldg(&a.in_rp[u + 1]);
         float acc[V] = {};
-#pragma unroll RefTune<KT>::UNR
-        for (int e = __ldg(&a.in_rp[u]); e < e1; ++e) {
-          float t[V];
-          ldf<V>(a.ze_in + (size_t)__ldg(&a.in_ci[e]) * KT + slot * V, t);
-#pragma unroll
-          for (int q = 0; q < V; ++q) acc[q] += t[q];
-        }
-        refine_epilogue<KT>(a, u, slot, acc, res);
+#pragma unroll RefTune<KT, T>::UNR
+        for (int e = __ldg(&a.in_rp[u]); e < e1; ++e)
+          add_raw<T, V>(acc, ld_raw<T, V>(z + (size_t)__ldg(&a.in_ci[e]) * KT + slot * V));
+        refine_epilogue<KT, T>(a, u, slot, pre, acc, res);
       }
     }
   }
@@ -186,30 +327,42 @@ __global__ void __launch_bounds__(256, RefTune<KT>::MIN_BLOCKS) refine_pass_kern
   }
 }
 
+// z_e of the BF16 passes into FP32 (exact) for the FP32 passes that follow
+__global__ void bf16_to_f32_kernel(int64_t count, const bf16* __restrict__ in, float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = __bfloat162float(in[i]);
+}
+
+template <typename T>
+__device__ __forceinline__ void st_one(T* p, float v) {
+  if constexpr (std::is_same<T, float>::value) *p = v;
+  else *p = __float2bfloat16_rn(v);
+}
+
 // r of a push state: rf = alpha r_push (FP32), first correction e1 = rf
-template <int KT>
+template <int KT, typename T>
 __global__ void refine_setup_push_kernel(int64_t n, const u64* __restrict__ r_push, double alpha,
                                          const int32_t* __restrict__ deg, float one_minus_alpha, float* __restrict__ rf,
-                                         float* __restrict__ ze) {
+                                         T* __restrict__ ze) {
   const int64_t total = n * KT;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const float v = (float)((double)r_push[i] * (alpha / kFixOne));
     rf[i] = v;
-    ze[i] = v * (one_minus_alpha / (float)deg[i / KT]);
+    st_one<T>(ze + i, v * (one_minus_alpha / (float)deg[i / KT]));
   }
 }
 
 // r of X after one exact pass X': rf = X' - X (exact signed difference, then FP32)
-template <int KT>
+template <int KT, typename T>
 __global__ void refine_setup_resid_kernel(int64_t n, const u64* __restrict__ x_new, const u64* __restrict__ x,
                                           const int32_t* __restrict__ deg, float one_minus_alpha,
-                                          float* __restrict__ rf, float* __restrict__ ze) {
+                                          float* __restrict__ rf, T* __restrict__ ze) {
   const int64_t total = n * KT;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const long long dlt = (long long)(x_new[i] - x[i]);
     const float v = (float)((double)dlt * (1.0 / kFixOne));
     rf[i] = v;
-    ze[i] = v * (one_minus_alpha / (float)deg[i / KT]);
+    st_one<T>(ze + i, v * (one_minus_alpha / (float)deg[i / KT]));
   }
 }
 
