@@ -321,7 +321,7 @@ def run_gpu(args):
         # dominant kernel: the FP32 correction pass (the Q1.63 passes only certify)
         avg_sweep_ms = fp32_ms / fp32_launches
         per_launch = fp32_pass_bytes(n, m, kt)
-        kernel_name = f"refine_pass_kernel<{kt}>"
+        kernel_name = f"refine_pass_kernel<{kt}, float>"
     else:
         avg_sweep_ms = sweep_ms / max(sweep_launches, 1)
         per_launch = sweep_bytes(n, m, kt)
