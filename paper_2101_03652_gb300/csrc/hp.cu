@@ -425,6 +425,8 @@ struct RefineTile {
   bool fp32_only = false;    // no BF16 stage
 };
 
+constexpr float kRelax = 1.1f;  // over-relaxation of in-place correction passes
+
 // Sweep phase with correction passes (see refine_kernel.cuh).  Buffers:
 // pi = X (Q1.63 base); r = the push residue, then e of the correction passes,
 // then X' of the exact pass; zb = [r_f f32 | z_e]; za = the second z_e buffer,
@@ -516,6 +518,13 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
     ++launches;
   }
   double rate = -1.0;  // observed contraction per pass
+  // In-place correction passes are over-relaxed (e <- e + w (e' - e), w = 1.1:
+  // SOR on the e-system, measured 11 % faster on R-MAT scale 20).  Modes with
+  // negative eigenvalues (near-bipartite structure) contract more slowly under
+  // w > 1, so the first stalled batch turns relaxation off for the query.
+  // Synchronous measured passes are never relaxed; every stop is certified by
+  // an exact pass whatever w does.
+  float relax = kRelax;
   for (int cycle = 0;; ++cycle) {
     if (cycle >= 8) {
       set_error("refinement did not certify within 8 cycles");
@@ -562,6 +571,9 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
         // rows without in-edges keep z_e = r_f (1-alpha)/d from the setup; the
         // synchronous pass rewrites every row of the other buffer
         ra.n_items = last ? fp->n_items_all : fp->n_items_nz;
+        // the passes before a learned correction stay plain: the model was
+        // trained on the state that plain passes reach
+        ra.relax = (last || corr_pending) ? 1.f : relax;
         if (prec == 0)
           refine_pass_kernel<KT, bf16><<<grids[0], 256, 0, st>>>(ra);
         else
@@ -595,6 +607,11 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
         rate = std::min(1.0 - alpha, std::max(0.05, std::pow(Fm / F, 1.0 / S)));
       F = Fm;
       if (corr_pending) break;
+      if (stalled && relax != 1.f) {
+        relax = 1.f;  // retry the stage without over-relaxation
+        rate = -1.0;
+        continue;
+      }
       if (stalled) {
         if (prec == 1) break;
         if (F > goal) {

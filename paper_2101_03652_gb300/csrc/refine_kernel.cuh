@@ -36,6 +36,7 @@ struct RefArgs {
   const float* rf;     // r of the cycle
   float* e_out;        // e of this pass (NULL: not written)
   float one_minus_alpha;
+  float relax;         // in-place passes: z_e <- z_e + relax (z_e' - z_e); 1 = plain
   const int32_t* npieces;
   float* heavy_acc;
   unsigned int* heavy_cnt;
@@ -183,7 +184,7 @@ constexpr bool kPrefetchRow = sizeof(T) == 2;
 template <int KT, typename T>
 __device__ __forceinline__ RowPre<RLay<KT, T>::V> refine_prefetch(const RefArgs& a, int u, int slot) {
   constexpr int V = RLay<KT, T>::V;
-  RowPre<V> p;
+  RowPre<V> p{};
   if constexpr (kPrefetchRow<T>) {
     ld_f32<V>(a.rf + (size_t)u * KT + slot * V, p.r);
     p.d = (float)__ldg(&a.deg[u]);
@@ -215,6 +216,13 @@ __device__ __forceinline__ void refine_epilogue(const RefArgs& a, int u, int slo
   for (int q = 0; q < V; ++q) {
     e[q] = r[q] + acc[q];
     zn[q] = e[q] * share;
+  }
+  if (a.relax != 1.f) {
+    // over-relaxed in-place pass (ze_in == ze_out): this row's own old value
+    float zo[V];
+    ld_row<T, V>(static_cast<const T*>(a.ze_in) + base, zo);
+#pragma unroll
+    for (int q = 0; q < V; ++q) zn[q] = zo[q] + a.relax * (zn[q] - zo[q]);
   }
   if (a.resid) {
     float zo[V];
