@@ -109,9 +109,10 @@ def sweep_bytes(n: int, m: int, kt: int) -> int:
 
 
 def fp32_pass_bytes(n: int, m: int, kt: int) -> int:
-    """Algorithmic bytes of one FP32 correction pass: in-CSR (4(n+1) + 4m),
-    degrees (4n), z_e gathered once and written once and r_f read once (12 n kt)."""
-    return 4 * (n + 1) + 4 * m + 4 * n + 12 * n * kt
+    """Algorithmic bytes of one (over-relaxed, in-place) FP32 correction pass:
+    in-CSR (4(n+1) + 4m), degrees (4n), z_e gathered once, the row's own old
+    z_e read once (the relaxation), z_e written once and r_f read once (16 n kt)."""
+    return 4 * (n + 1) + 4 * m + 4 * n + 16 * n * kt
 
 
 TRAFFIC_FILES = {
