@@ -339,12 +339,15 @@ struct WalkArgs {
 
 // Each thread runs kWalksPerThread consecutive walk ids, so the start node
 // advances monotonically (one binary search per thread) and a warp waits for
-// the longest of its threads' walk *sums* rather than of single walks.  A
-// thread merges consecutive endpoints at the same node before its atomics.
+// the longest of its threads' walk *sums* rather than of single walks.  The
+// walks are taken kWalkLanes at a time, stepped in lockstep, so that their
+// random loads (row pointers, then the column index) are in flight together.
+// A thread merges consecutive endpoints at the same node before its atomics.
 constexpr int kWalksPerThread = 16;
+constexpr int kWalkLanes = 2;
 
 template <int KT>
-__global__ void __launch_bounds__(256) walk_kernel(WalkArgs a) {
+__global__ void __launch_bounds__(256, 6) walk_kernel(WalkArgs a) {
   const int c = blockIdx.y;
   const int64_t* offs = a.offs + (size_t)c * (a.n + 1);
   const int64_t total = offs[a.n];
@@ -361,50 +364,84 @@ __global__ void __launch_bounds__(256) walk_kernel(WalkArgs a) {
     int32_t pend_u = -1;
     unsigned pend_n = 0;
     double pend_est = 0.0;
-    for (int64_t w = w_begin; w < w_end; ++w) {
-      while (offs[o + 1] <= w) ++o;
-      const int32_t v = a.new_of_old[o];
-      const double rv = (double)a.r[(size_t)v * KT + c];
-      const double inc = rv / (double)(offs[o + 1] - offs[o]);
-      int32_t cur = v;
-      uint4 words = make_uint4(0, 0, 0, 0);
-      int32_t t = 0;
-      bool ok = true;
-      for (;;) {
-        if ((t & 1) == 0)
-          words = philox4x32_10(make_uint4((uint32_t)w, (uint32_t)((u64)w >> 32), (uint32_t)(t >> 1),
-                                           (uint32_t)(a.col0 + c)),
-                                a.key0, a.key1);
-        const uint32_t stopw = (t & 1) ? words.z : words.x;
-        const uint32_t movew = (t & 1) ? words.w : words.y;
-        if (stopw < a.stop_below) break;
-        if (t >= a.max_steps) { ok = false; break; }
-        const int32_t e0 = __ldg(&a.out_rp[cur]);
-        const int32_t d = __ldg(&a.out_rp[cur + 1]) - e0;
-        cur = __ldg(&a.out_ci[e0 + (int32_t)__umulhi(movew, (uint32_t)d)]);
-        ++t;
-      }
-      if (!ok) {
-        atomicExch(a.status, 1);
-        continue;
-      }
-      moves += (u64)t;
-      if (cur != pend_u) {
-        if (pend_n) {
-          atomicAdd(&a.counts[(size_t)pend_u * KT + c], pend_n);
-          atomicAdd(&a.est[(size_t)pend_u * KT + c], pend_est);
+    bool failed = false;
+    for (int64_t w0 = w_begin; w0 < w_end; w0 += kWalkLanes) {
+      int32_t cur[kWalkLanes];
+      double inc[kWalkLanes];
+      int32_t t[kWalkLanes];
+      bool live[kWalkLanes];
+      uint4 words[kWalkLanes];
+#pragma unroll
+      for (int j = 0; j < kWalkLanes; ++j) {
+        const int64_t w = w0 + j;
+        live[j] = w < w_end;
+        t[j] = 0;
+        cur[j] = 0;
+        inc[j] = 0.0;
+        words[j] = make_uint4(0, 0, 0, 0);
+        if (live[j]) {
+          while (offs[o + 1] <= w) ++o;
+          const int32_t v = a.new_of_old[o];
+          const double rv = (double)a.r[(size_t)v * KT + c];
+          inc[j] = rv / (double)(offs[o + 1] - offs[o]);
+          cur[j] = v;
         }
-        pend_u = cur;
-        pend_n = 0;
-        pend_est = 0.0;
       }
-      pend_n += 1;
-      pend_est += inc;
+      bool any = true;
+      while (any) {
+        any = false;
+#pragma unroll
+        for (int j = 0; j < kWalkLanes; ++j) {
+          if (!live[j]) continue;
+          const int64_t w = w0 + j;
+          if ((t[j] & 1) == 0)
+            words[j] = philox4x32_10(make_uint4((uint32_t)w, (uint32_t)((u64)w >> 32), (uint32_t)(t[j] >> 1),
+                                                (uint32_t)(a.col0 + c)),
+                                     a.key0, a.key1);
+          const uint32_t stopw = (t[j] & 1) ? words[j].z : words[j].x;
+          if (stopw < a.stop_below) { live[j] = false; t[j] = -t[j] - 1; continue; }  // stopped: t < 0
+          if (t[j] >= a.max_steps) { live[j] = false; failed = true; t[j] = -t[j] - 1; continue; }
+          any = true;
+        }
+        // the moves of the walks still running, their loads issued together
+        int32_t e0[kWalkLanes], d[kWalkLanes];
+#pragma unroll
+        for (int j = 0; j < kWalkLanes; ++j)
+          if (live[j]) {
+            e0[j] = __ldg(&a.out_rp[cur[j]]);
+            d[j] = __ldg(&a.out_rp[cur[j] + 1]) - e0[j];
+          }
+#pragma unroll
+        for (int j = 0; j < kWalkLanes; ++j)
+          if (live[j]) {
+            const uint32_t movew = (t[j] & 1) ? words[j].w : words[j].y;
+            cur[j] = __ldg(&a.out_ci[e0[j] + (int32_t)__umulhi(movew, (uint32_t)d[j])]);
+            ++t[j];
+          }
+      }
+      // endpoints in walk-id order
+#pragma unroll
+      for (int j = 0; j < kWalkLanes; ++j) {
+        if (w0 + j >= w_end) continue;
+        moves += (u64)(-t[j] - 1);
+        if (cur[j] != pend_u) {
+          if (pend_n) {
+            atomicAdd(&a.counts[(size_t)pend_u * KT + c], pend_n);
+            atomicAdd(&a.est[(size_t)pend_u * KT + c], pend_est);
+          }
+          pend_u = cur[j];
+          pend_n = 0;
+          pend_est = 0.0;
+        }
+        pend_n += 1;
+        pend_est += inc[j];
+      }
     }
     if (pend_n) {
       atomicAdd(&a.counts[(size_t)pend_u * KT + c], pend_n);
       atomicAdd(&a.est[(size_t)pend_u * KT + c], pend_est);
     }
+    if (failed) atomicExch(a.status, 1);
   }
 #pragma unroll
   for (int off = 16; off; off >>= 1) moves += __shfl_xor_sync(kAllLanes, moves, off);
