@@ -342,3 +342,26 @@ def test_bf16_stage_is_certified(P, c0, lam):
         assert np.abs(pi[i] - exact).sum() <= 2 * lam
     if lam >= 1e-2:
         assert st[0]["bf16_passes"] > 0
+
+
+@pytest.mark.parametrize("graph", ["bipartite", "even_cycle"])
+def test_relaxation_fallback_on_bipartite_graphs(P, graph):
+    """Bipartite graphs give (1-alpha) P the eigenvalue -(1-alpha), the mode
+    that over-relaxed passes amplify: the stalled batch must turn relaxation
+    off and the answer must still be certified and match the exact vector."""
+    if graph == "bipartite":
+        a, b = 40, 60
+        edges = [(i, a + j) for i in range(a) for j in range(b)] + [(a + j, i) for j in range(b) for i in range(a)]
+        n = a + b
+    else:
+        n = 1000
+        edges = [(i, (i + 1) % n) for i in range(n)] + [(i, (i - 1) % n) for i in range(n)]
+    rp, ci = gen.from_edges(n, edges)
+    og = O.Graph(rp, ci)
+    src = np.array([0, 7, n - 1], dtype=np.int32)
+    for kw in ({}, {"switch_edges": 0}):
+        pi, st = run(P, rp, ci, src, k_tile=4, **kw)
+        check_bound_and_mass(st)
+        for i, s in enumerate(src):
+            exact = O.dense_solve(og, int(s), ALPHA) if n <= 200 else O.powitr(og, int(s), ALPHA, 1e-13)[0]
+            assert np.abs(pi[i] - exact).sum() <= 2 * LAM, (graph, kw, i)
