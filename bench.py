@@ -36,6 +36,7 @@ WORKLOADS = {
     "rmat20-k16": (20, 16, 16, 16),
     "rmat20-k8": (20, 16, 8, 8),
     "rmat22-k1": (22, 16, 1, 1),
+    "rmat22-k64": (22, 16, 64, 64),
     "rmat22-approx": (22, 16, 16, 16),  # SpeedPPR, eps = 0.5, sources seed 3
     "rmat22-index": (22, 16, 16, 16),   # SpeedPPR-Index (walks read from the index), same sources
 }
@@ -240,6 +241,15 @@ def run_gpu(args):
         g.build_index(0x1DE5, ALPHA)
         opts["flags"] = P.PPR_FLAG_INDEX
     mode = P.PPR_APPROX if approx else P.PPR_HP
+    tuned = None
+    if not approx and not args.no_autotune:
+        # the k-tile and the queue->pass switch come from the library's
+        # autotuner, run on this step's sources outside the timed region
+        t_tune = time.perf_counter()
+        kt_t, sw_t, _ = g.autotune(src, lam=LAMBDA, alpha=ALPHA)
+        tuned = {"k_tile": int(kt_t), "switch_edges": int(sw_t), "seconds": time.perf_counter() - t_tune}
+        opts = dict(lam=LAMBDA, alpha=ALPHA, k_tile=0, switch_edges=-1)
+        kt = int(kt_t)
 
     def step(out_buf):
         return g.query(src, mode, out_pi=out_buf, **opts)[1]
@@ -357,7 +367,7 @@ def run_gpu(args):
         "config": {"workload": args.workload, "graph": f"R-MAT scale {WORKLOADS[args.workload][0]}, "
                    f"edge factor {WORKLOADS[args.workload][1]}, a/b/c/d 0.57/0.19/0.19/0.05",
                    "n": n, "m": m, "alpha": ALPHA, ("eps" if approx else "lambda"): (EPS if approx else LAMBDA),
-                   "sources_per_step": k, "k_tile": kt,
+                   "sources_per_step": k, "k_tile": kt, "autotuned": tuned,
                    "l2": "256 MB buffer written between timed steps", "parallelism": f"replicas x{ws}"},
         "sweeps_per_tile": statistics.median(sweeps),
         "e2e": {"value": ws * k * e2e_steps / e2e_total, "unit": "queries/s", "h2d_bytes_per_step": 4 * k,
@@ -577,6 +587,7 @@ def main():
     ap.add_argument("--sweep-scale", type=int, default=20, help="R-MAT scale of the eps-sweep study")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the oracle CPU baseline")
     ap.add_argument("--skip-warm", action="store_true", help="omit the learned warm-start comparison")
+    ap.add_argument("--no-autotune", action="store_true", help="use the workload's fixed k-tile and the default switch")
     ap.add_argument("--serve-scale", type=int, default=25, help="R-MAT scale of the serving workload")
     ap.add_argument("--serve-ef", type=int, default=32)
     ap.add_argument("--serve-train", type=int, default=2048)
