@@ -517,7 +517,7 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
                                                                    static_cast<float*>(zbuf_a));
     ++launches;
   }
-  double rate = -1.0;  // observed contraction per pass
+  double rates[2] = {-1.0, -1.0};  // observed contraction per pass, BF16 / FP32
   // In-place correction passes are over-relaxed (e <- e + w (e' - e), w = 1.15:
   // SOR on the e-system; on R-MAT scale 20 and a Chung-Lu graph of 200,000
   // nodes w = 1.15 measured fastest, 1.2 and above slower).  Modes with
@@ -550,9 +550,13 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
         prec = 1;
         continue;
       }
-      const double cr = rate > 0.0 ? rate : (1.0 - alpha);
+      // a precision without a rate of its own borrows the other's; only when
+      // neither is known does a short first batch learn one
+      double& rate = rates[prec];
+      const double known = rate > 0.0 ? rate : rates[1 - prec];
+      const double cr = known > 0.0 ? known : (1.0 - alpha);
       int S = std::max((int)std::ceil(std::log(phase_goal / F) / std::log(cr) - 1e-12), 1);
-      if (rate <= 0.0) S = std::min(S, 16);  // learn the rate first
+      if (known <= 0.0) S = std::min(S, 16);  // learn the rate first
       if (corr_pending) S = t.corr;          // the passes the correction model was trained after
       if (sweeps + S + 1 > t.max_sweeps) {
         set_error("sweep limit %d reached", t.max_sweeps);
@@ -610,7 +614,7 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
       if (corr_pending) break;
       if (stalled && relax != 1.f) {
         relax = 1.f;  // retry the stage without over-relaxation
-        rate = -1.0;
+        rates[0] = rates[1] = -1.0;
         continue;
       }
       if (stalled) {
@@ -640,7 +644,7 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
         PPR_TRY(warm_correct_tile(t.model, g, t.src_new, ncols, KT, alpha, X, t.mass, za, X, st));
         launches += 2;
         corr_pending = false;
-        rate = -1.0;  // the correction changes the error: learn the rate again
+        rates[0] = rates[1] = -1.0;  // the correction changes the error: learn the rates again
       }
     }
 
