@@ -139,9 +139,18 @@ ppr_status ppr_graph_load(const int64_t* row_ptr, const int32_t* col_idx, int64_
  *             returned pi_hat; APPROX = the FP32 residue the walks started from.
  *   out_walk_counts: optional k x n uint32 (APPROX only) walk endpoint counts.
  *   stats   : optional host array of k entries.
- * HP mode follows Algorithm 3 (frontier push, then sweeps); APPROX follows
- * Algorithm 4.  Work runs on `cuda_stream`; the call returns after the stream
- * has finished the query.  Errors: PPR_ERR_ARG, PPR_ERR_ADMIT (state does not
+ * HP mode follows Algorithm 3: a frontier push (the queue phase) until a
+ * level's out-edges exceed the switch threshold, then dense pull passes.  By
+ * default the dense phase is an iterative refinement: the remaining error
+ * e = pi - X of the Q1.63 estimate X (the push reserve) solves
+ * e = r + (1-alpha) e P (Eq. 7 with r in place of alpha e_s), which BF16 and
+ * FP32 passes solve (in place, over-relaxed), then e is folded into X and one
+ * exact synchronous Q1.63 pass measures ||X' - X||_1; the returned X' has
+ * ||pi_hat - pi||_1 <= (1-alpha) ||X' - X||_1 / alpha + rounding <= lambda
+ * (stats[i].final_l1_residual).  Flags select the other dense phases (all
+ * passes Q1.63, synchronous PowItr passes, Algorithm 3's epochs).  APPROX
+ * follows Algorithm 4.  Work runs on `cuda_stream`; the call returns after
+ * the stream has finished the query.  Errors: PPR_ERR_ARG, PPR_ERR_ADMIT (state does not
  * fit in free device memory), PPR_ERR_NOT_CONVERGED, PPR_ERR_OOM, PPR_ERR_CUDA.
  */
 ppr_status ppr_sssp_query(ppr_graph* g, const int32_t* src, int32_t k, ppr_mode mode,
