@@ -88,14 +88,15 @@ def test_fig1_graph_approx(P):
 
 
 def test_rmat22_configuration_sampled(P):
-    """R-MAT scale 22 (the approximate workload's graph): two sources, counts
-    bit-exact for one of them, guarantees checked for both."""
+    """R-MAT scale 22, the approximate workload's launch (16 sources in one
+    16-column tile): counts bit-exact for a sampled source, walk budget and
+    mass checked for all."""
     rp, ci = gen.rmat(22, 16, seed=1)
     og = O.Graph(rp, ci)
-    src = gen.sources(len(rp) - 1, 2, seed=3)
-    pi, r, counts, st = run_approx(P, rp, ci, src, k_tile=2)
+    src = gen.sources(len(rp) - 1, 16, seed=3)
+    pi, r, counts, st = run_approx(P, rp, ci, src, k_tile=16)
     d = np.diff(rp)
-    for i in range(2):
+    for i in range(len(src)):
         assert np.all(r[i] <= d / st[i]["W"] * (1 + 1e-6))
         assert st[i]["walks"] <= og.m + og.n
         assert abs(pi[i].sum() - 1.0) < 1e-4

@@ -179,11 +179,16 @@ def rmat20():
 
 
 def test_rmat20_bench_configuration(P, rmat20):
-    """The benchmark's launch: 64 sources, k_tile 8.  Two sampled sources are
-    checked against the oracle in full; every source satisfies the certified
-    bound and the mass identity."""
+    """The benchmark's launch: 64 sources in one 64-column tile with the
+    autotuned switch threshold.  Two sampled sources are checked against the
+    oracle in full; every source satisfies the certified bound and the mass
+    identity."""
     rp, ci, src = rmat20
-    pi, st = run(P, rp, ci, src, k_tile=8)
+    g = P.Graph(rp, ci)
+    kt, sw, _ = g.autotune(src, lam=LAM)
+    g.close()
+    assert kt in (1, 2, 4, 8, 16, 32, 64) and sw >= 0
+    pi, st = run(P, rp, ci, src, k_tile=kt, switch_edges=sw)
     check_bound_and_mass(st)
     og = O.Graph(rp, ci)
     for i in (0, 37):
@@ -365,3 +370,17 @@ def test_relaxation_fallback_on_bipartite_graphs(P, graph):
         for i, s in enumerate(src):
             exact = O.dense_solve(og, int(s), ALPHA) if n <= 200 else O.powitr(og, int(s), ALPHA, 1e-13)[0]
             assert np.abs(pi[i] - exact).sum() <= 2 * LAM, (graph, kw, i)
+
+
+def test_rmat22_hp_bench_configuration(P):
+    """R-MAT scale 22, 64 sources in one 64-column tile (the 64-source HP
+    workload): every source certified, one sampled source against the oracle
+    in full."""
+    rp, ci = gen.rmat(22, 16, seed=1)
+    src = gen.sources(len(rp) - 1, 64, seed=2)
+    pi, st = run(P, rp, ci, src, k_tile=64)
+    check_bound_and_mass(st)
+    assert np.all(pi >= 0)
+    og = O.Graph(rp, ci)
+    ref, _, _ = O.powerpush(og, int(src[0]), ALPHA, LAM)
+    assert np.abs(pi[0] - ref).sum() <= 2 * LAM
