@@ -108,13 +108,27 @@ __global__ void __launch_bounds__(256) project_kernel(int32_t n, const float* __
   float acc[NJ];
 #pragma unroll
   for (int q = 0; q < NJ; ++q) acc[q] = 0.f;
+  __shared__ int row_nz[64];
   for (int64_t r0 = (int64_t)blockIdx.x * 64; r0 < n; r0 += (int64_t)gridDim.x * 64) {
+    for (int t = threadIdx.x; t < 64 * B; t += blockDim.x) {
+      const int row = t / B, cc = t % B;
+      Ss[row][cc] = (r0 + row < n) ? S[(size_t)(r0 + row) * B + cc] : 0.f;
+    }
+    __syncthreads();
+    // the sketch is zero outside the sources' 2-hop balls: G rows are made
+    // only where some column of S is nonzero
+    if (threadIdx.x < 64) {
+      int nz = 0;
+      for (int cc = 0; cc < B; ++cc) nz |= Ss[threadIdx.x][cc] != 0.f;
+      row_nz[threadIdx.x] = nz;
+    }
+    __syncthreads();
     // 64 rows x 32 Philox calls, 8 calls per thread
     for (int t = threadIdx.x; t < 64 * (F / 4); t += blockDim.x) {
       const int row = t / (F / 4), q = t % (F / 4);
       const int64_t u = r0 + row;
       float z[4] = {0.f, 0.f, 0.f, 0.f};
-      if (u < n) {
+      if (u < n && row_nz[row]) {
         const uint4 w = philox10(make_uint4((uint32_t)old_of_new[u], (uint32_t)q, 0x47u, 0u), k0, k1);
         const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
@@ -130,10 +144,6 @@ __global__ void __launch_bounds__(256) project_kernel(int32_t n, const float* __
       }
 #pragma unroll
       for (int p = 0; p < 4; ++p) Gs[row][4 * q + p] = z[p];
-    }
-    for (int t = threadIdx.x; t < 64 * B; t += blockDim.x) {
-      const int row = t / B, cc = t % B;
-      Ss[row][cc] = (r0 + row < n) ? S[(size_t)(r0 + row) * B + cc] : 0.f;
     }
     __syncthreads();
     for (int row = 0; row < 64; ++row) {
@@ -307,7 +317,10 @@ __global__ void __launch_bounds__(256) basis_kernel(BasisArgs a) {
         dz[j][i] = 0.f;
         const int u = r0 + (i >= 2 ? 8 : 0), c = j * 8 + kq + (i & 1);
         if (u >= a.n || c >= a.ncols) continue;
-        const float s = a.S[(size_t)u * B + c];
+        // the sketch enters Z only in the sketch form; otherwise it is read
+        // only as the fallback of a column whose sum is zero
+        const bool need_s = a.with_sketch || (PASS != 1 && !(a.sig[c] > 0.f));
+        const float s = need_s ? a.S[(size_t)u * B + c] : 0.f;
         const float z = acc[j][i] + (a.with_sketch ? s : 0.f);
         const float y = fmaxf(z, 0.f);
         if constexpr (PASS == 1) {
