@@ -648,27 +648,50 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
       }
     }
 
-    // ---- one exact synchronous pass from X
-    PPR_CUDA_TRY(cudaMemsetAsync(resid, 0, 64 * 8, st));
-    sa.z_in = za;
-    sa.z_out = nullptr;
-    sa.x_out = Xn;
-    sa.n_items = plan.n_items_all;
-    sa.resid = resid;
-    PPR_CUDA_TRY(cudaEventRecord(es0, st));
-    sweep_kernel<KT><<<sweep_grid, 256, 0, st>>>(sa);
-    PPR_CUDA_TRY(cudaEventRecord(es1, st));
-    PPR_CUDA_TRY(cudaGetLastError());
-    ++sweeps;
-    ++launches;
-    ++ro.cycles;
-    PPR_CUDA_TRY(cudaMemcpyAsync(hpin, resid, 64 * 8, cudaMemcpyDeviceToHost, st));
-    PPR_CUDA_TRY(cudaStreamSynchronize(st));
-    {
+    // ---- one exact synchronous pass from X.  When the last measured F puts
+    // the coming bound far above lambda, the pass also sets up the next cycle
+    // (r = X' - X exactly, in the precision that cycle will start in) instead
+    // of writing X'; should it certify after all, a plain pass from the same
+    // X produces X'.
+    const bool measured = !(warm_x0 && cycle == 0) && ran;
+    const double predicted_bound = (1.0 - alpha) * (1.0 - alpha) * F / alpha;
+    bool fused = measured && predicted_bound > 4.0 * lambda;
+    const int prec_next = cycle_prec((1.0 - alpha) * F);
+    for (;;) {
+      PPR_CUDA_TRY(cudaMemsetAsync(resid, 0, 64 * 8, st));
+      sa.z_in = za;
+      sa.z_out = nullptr;
+      sa.x_out = fused ? nullptr : Xn;
+      sa.x_base = fused ? X : nullptr;
+      sa.rf_next = fused ? rf : nullptr;
+      sa.ze_next = fused ? zbuf_a : nullptr;
+      sa.ze_bf16 = prec_next == 0;
+      sa.n_items = plan.n_items_all;
+      sa.resid = resid;
+      PPR_CUDA_TRY(cudaEventRecord(es0, st));
+      sweep_kernel<KT><<<sweep_grid, 256, 0, st>>>(sa);
+      PPR_CUDA_TRY(cudaEventRecord(es1, st));
+      PPR_CUDA_TRY(cudaGetLastError());
+      ++sweeps;
+      ++launches;
+      PPR_CUDA_TRY(cudaMemcpyAsync(hpin, resid, 64 * 8, cudaMemcpyDeviceToHost, st));
+      PPR_CUDA_TRY(cudaStreamSynchronize(st));
       float a_ms = 0.f;
       cudaEventElapsedTime(&a_ms, es0, es1);
       ms_sweep += a_ms;
+      if (!fused) break;
+      // certified after all: X' is needed, so run the plain pass
+      const double* Dq = reinterpret_cast<const double*>(hpin);
+      bool ok_q = true;
+      for (int c = 0; c < ncols; ++c)
+        if ((1.0 - alpha) * (Dq[c] / kFixOne / alpha) * (1.0 + 1e-4) + 2.0 * slack > lambda) ok_q = false;
+      if (!ok_q) break;
+      fused = false;
     }
+    sa.x_base = nullptr;
+    sa.rf_next = nullptr;
+    sa.ze_next = nullptr;
+    ++ro.cycles;
     const double* D = reinterpret_cast<const double*>(hpin);
     bool ok = true;
     F0 = 0.0;
@@ -680,6 +703,10 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
       if (warm_x0 && cycle == 0) r0[c] = Dc;  // measured ||r(x0)||_1 of the model's estimate
     }
     if (ok) return PPR_OK;
+    if (fused) {
+      prec0 = prec_next;  // the pass wrote r and z_e of the next cycle
+      continue;
+    }
     // next cycle from X: r = X' - X, z_e in the precision the cycle starts in
     prec0 = cycle_prec(F0);
     if (prec0 == 0)

@@ -4,6 +4,8 @@
 // for a tile of KT sources at once.  Values are Q1.63 fixed point.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "ppr_internal.cuh"
 
 namespace ppr {
@@ -36,6 +38,14 @@ struct SweepArgs {
   const int32_t* heavy_npieces;
   u64* heavy_acc;
   unsigned int* heavy_cnt;
+  // measuring pass that also sets up the next refinement cycle (x_base not
+  // NULL): r = x' - x_base exactly, its l1 norm into resid, r as FP32 into
+  // rf_next and r (1-alpha)/d into ze_next (FP32, or BF16 when ze_bf16);
+  // neither z_out nor x_out is written
+  const u64* x_base = nullptr;
+  float* rf_next = nullptr;
+  void* ze_next = nullptr;
+  int ze_bf16 = 0;
 };
 
 constexpr int kItemPeriods = 16;  // target cost of one work item (see build_plan)
@@ -73,8 +83,27 @@ template <int KT>
 __device__ __forceinline__ void row_epilogue(const SweepArgs& a, int u, int slot, const u64 (&acc)[Lay<KT>::V],
                                              float (&res)[Lay<KT>::V]) {
   constexpr int V = Lay<KT>::V;
-  const u64 om = __ldg(&a.omega[u]);
   const float iw = __ldg(&a.invw[u]);
+  if (a.x_base) {
+    const size_t base = (size_t)u * KT + slot * V;
+    u64 xo[V];
+    ld_vec<V>(a.x_base + base, xo);
+    const float share = 1.f / iw;
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      const u64 xn = acc[q] + (u == a.src[slot * V + q] ? a.alpha_raw : 0ull);
+      const long long d = (long long)(xn - xo[q]);
+      res[q] += (float)(d < 0 ? -d : d);
+      const float rv = (float)((double)d * (1.0 / kFixOne));
+      a.rf_next[base + q] = rv;
+      if (a.ze_bf16)
+        static_cast<__nv_bfloat16*>(a.ze_next)[base + q] = __float2bfloat16_rn(rv * share);
+      else
+        static_cast<float*>(a.ze_next)[base + q] = rv * share;
+    }
+    return;
+  }
+  const u64 om = __ldg(&a.omega[u]);
   u64 zn[V], xn[V];
 #pragma unroll
   for (int q = 0; q < V; ++q) {
