@@ -79,3 +79,25 @@ def test_no_cpu_fallback_without_device():
     with pytest.raises(P.PPRError) as e:
         P.ppr_graph_load(rp, ci)
     assert e.value.status == binding.PPR_ERR_CUDA
+
+
+def test_binding_constants_match_the_header():
+    """Flags, statuses and modes in the binding are the header's values."""
+    text = open(os.path.join(ROOT, "include", "ppr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    defines = {k: int(v) for k, v in re.findall(r"#define\s+(PPR_FLAG_[A-Z0-9_]+)\s+(\d+)", text)}
+    enums = {k: int(v) for k, v in re.findall(r"\b(PPR_(?:OK|ERR_[A-Z_]+|HP|APPROX))\s*=\s*(-?\d+)", text)}
+    assert len(defines) >= 6 and len(enums) >= 9
+    for name, value in {**defines, **enums}.items():
+        assert getattr(binding, name) == value, name
+    flags = list(defines.values())
+    assert len(set(flags)) == len(flags) and all(f & (f - 1) == 0 for f in flags)  # distinct single bits
+
+
+def test_stats_layout_matches_the_header():
+    """ppr_stats: the binding's fields, in order, are the header's."""
+    text = open(os.path.join(ROOT, "include", "ppr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\} ppr_stats;", text, flags=re.S).group(1)
+    fields = re.findall(r"\b(?:int32_t|int64_t|double)\s+([A-Za-z_0-9]+)\s*;", body)
+    assert [f for f, _ in binding.ppr_stats._fields_] == fields
