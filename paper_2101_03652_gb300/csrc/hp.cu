@@ -442,11 +442,13 @@ struct RefineOut {
 };
 
 template <int KT, typename T>
-static ppr_status refine_kernel_setup(ppr_graph* g, Plan** plan, int* grid, cudaStream_t st) {
+static ppr_status refine_kernel_setup(ppr_graph* g, Plan** plan, int* grid, int* grid_meas, cudaStream_t st) {
   PPR_TRY(get_plan(g, RLay<KT, T>::L, plan, st));
   int bps = 0;
-  PPR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, refine_pass_kernel<KT, T>, 256, 0));
+  PPR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, refine_pass_kernel<KT, T, false>, 256, 0));
   *grid = sm_count() * std::max(bps, 1);
+  PPR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, refine_pass_kernel<KT, T, true>, 256, 0));
+  *grid_meas = sm_count() * std::max(bps, 1);
   return PPR_OK;
 }
 
@@ -470,9 +472,9 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
   const float oma = (float)(1.0 - alpha);
 
   Plan* plans[2] = {nullptr, nullptr};
-  int grids[2] = {0, 0};
-  PPR_TRY((refine_kernel_setup<KT, bf16>(g, &plans[0], &grids[0], st)));
-  PPR_TRY((refine_kernel_setup<KT, float>(g, &plans[1], &grids[1], st)));
+  int grids[2] = {0, 0}, grids_meas[2] = {0, 0};
+  PPR_TRY((refine_kernel_setup<KT, bf16>(g, &plans[0], &grids[0], &grids_meas[0], st)));
+  PPR_TRY((refine_kernel_setup<KT, float>(g, &plans[1], &grids[1], &grids_meas[1], st)));
   RefArgs ra;
   ra.in_rp = g->d_in_rp;
   ra.in_ci = g->d_in_ci;
@@ -579,10 +581,13 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
         // the passes before a learned correction stay plain: the model was
         // trained on the state that plain passes reach
         ra.relax = (last || corr_pending) ? 1.f : relax;
-        if (prec == 0)
-          refine_pass_kernel<KT, bf16><<<grids[0], 256, 0, st>>>(ra);
-        else
-          refine_pass_kernel<KT, float><<<grids[1], 256, 0, st>>>(ra);
+        if (prec == 0) {
+          if (last) refine_pass_kernel<KT, bf16, true><<<grids_meas[0], 256, 0, st>>>(ra);
+          else refine_pass_kernel<KT, bf16, false><<<grids[0], 256, 0, st>>>(ra);
+        } else {
+          if (last) refine_pass_kernel<KT, float, true><<<grids_meas[1], 256, 0, st>>>(ra);
+          else refine_pass_kernel<KT, float, false><<<grids[1], 256, 0, st>>>(ra);
+        }
       }
       PPR_CUDA_TRY(cudaEventRecord(es1, st));
       PPR_CUDA_TRY(cudaGetLastError());

@@ -52,14 +52,17 @@ struct RLay {
   static constexpr int EPW = 32 / L;
 };
 
+constexpr int kBf16FastBlocks = 5;
+
 // gathers in flight per lane and blocks per SM (measured on R-MAT scale 20):
 // FP32 rows: wide rows keep more gathers per warp, narrow ones more warps;
 // BF16 rows carry 8 columns per lane, whose sums need 64 registers
-template <int KT, typename T>
+template <int KT, typename T, bool MEAS>
 struct RefTune {
   static constexpr bool kBf16 = sizeof(T) == 2;
   static constexpr int UNR = kBf16 ? 8 : (RLay<KT, T>::L >= 8 ? 8 : 4);
-  static constexpr int MIN_BLOCKS = kBf16 ? 4 : (RLay<KT, T>::L >= 8 ? 6 : 8);
+  // passes without the residual sums need fewer registers
+  static constexpr int MIN_BLOCKS = kBf16 ? (MEAS ? 4 : kBf16FastBlocks) : (RLay<KT, T>::L >= 8 ? 6 : 8);
 };
 
 // raw 16-byte (or narrower) row piece of V values of T, converted to FP32 when summed
@@ -193,7 +196,7 @@ __device__ __forceinline__ RowPre<RLay<KT, T>::V> refine_prefetch(const RefArgs&
 }
 
 // finish row u: e = r + sum, ze = e (1-alpha) / d
-template <int KT, typename T>
+template <int KT, typename T, bool MEAS>
 __device__ __forceinline__ void refine_epilogue(const RefArgs& a, int u, int slot,
                                                 const RowPre<RLay<KT, T>::V>& pre,
                                                 const float (&acc)[RLay<KT, T>::V],
@@ -224,7 +227,7 @@ __device__ __forceinline__ void refine_epilogue(const RefArgs& a, int u, int slo
 #pragma unroll
     for (int q = 0; q < V; ++q) zn[q] = zo[q] + a.relax * (zn[q] - zo[q]);
   }
-  if (a.resid) {
+  if (MEAS) {
     float zo[V];
     ld_row<T, V>(static_cast<const T*>(a.ze_in) + base, zo);
     const float inv = d / a.one_minus_alpha;
@@ -238,7 +241,7 @@ __device__ __forceinline__ void refine_epilogue(const RefArgs& a, int u, int slo
 template <int KT, typename T>
 __device__ __forceinline__ void refine_gather_warp(const RefArgs& a, int e_begin, int e_end, int lane, int slot,
                                                    float (&acc)[RLay<KT, T>::V]) {
-  constexpr int V = RLay<KT, T>::V, L = RLay<KT, T>::L, EPW = RLay<KT, T>::EPW, UNR = RefTune<KT, T>::UNR;
+  constexpr int V = RLay<KT, T>::V, L = RLay<KT, T>::L, EPW = RLay<KT, T>::EPW, UNR = RefTune<KT, T, false>::UNR;
   const T* z = static_cast<const T*>(a.ze_in);
   for (int base = e_begin; base < e_end; base += EPW * UNR) {
     int v[UNR];
@@ -256,8 +259,9 @@ __device__ __forceinline__ void refine_gather_warp(const RefArgs& a, int e_begin
   }
 }
 
-template <int KT, typename T>
-__global__ void __launch_bounds__(256, (RefTune<KT, T>::MIN_BLOCKS)) refine_pass_kernel(RefArgs a) {
+// MEAS: the measured (synchronous) pass of a batch, which also sums |e' - e|
+template <int KT, typename T, bool MEAS>
+__global__ void __launch_bounds__(256, (RefTune<KT, T, MEAS>::MIN_BLOCKS)) refine_pass_kernel(RefArgs a) {
   constexpr int V = RLay<KT, T>::V, L = RLay<KT, T>::L;
   const int lane = threadIdx.x & 31;
   const int slot = lane % L;
@@ -290,7 +294,7 @@ __global__ void __launch_bounds__(256, (RefTune<KT, T>::MIN_BLOCKS)) refine_pass
           float tot[V];
 #pragma unroll
           for (int q = 0; q < V; ++q) tot[q] = atomicExch(&a.heavy_acc[(size_t)u * KT + slot * V + q], 0.f);
-          refine_epilogue<KT, T>(a, u, slot, refine_prefetch<KT, T>(a, u, slot), tot, res);
+          refine_epilogue<KT, T, MEAS>(a, u, slot, refine_prefetch<KT, T>(a, u, slot), tot, res);
         }
         if (lane == 0) atomicExch(&a.heavy_cnt[u], 0u);
       }
@@ -303,21 +307,21 @@ __global__ void __launch_bounds__(256, (RefTune<KT, T>::MIN_BLOCKS)) refine_pass
         for (int off = L; off < 32; off <<= 1)
 #pragma unroll
           for (int q = 0; q < V; ++q) acc[q] += __shfl_xor_sync(kFull, acc[q], off);
-        if (lane < L) refine_epilogue<KT, T>(a, u, slot, pre, acc, res);
+        if (lane < L) refine_epilogue<KT, T, MEAS>(a, u, slot, pre, acc, res);
       }
     } else {
       for (int u = w.y + lane / L; u < w.z; u += 32 / L) {
         const auto pre = refine_prefetch<KT, T>(a, u, slot);
         const int e1 = __ldg(&a.in_rp[u + 1]);
         float acc[V] = {};
-#pragma unroll RefTune<KT, T>::UNR
+#pragma unroll RefTune<KT, T, MEAS>::UNR
         for (int e = __ldg(&a.in_rp[u]); e < e1; ++e)
           add_raw<T, V>(acc, ld_raw<T, V>(z + (size_t)__ldg(&a.in_ci[e]) * KT + slot * V));
-        refine_epilogue<KT, T>(a, u, slot, pre, acc, res);
+        refine_epilogue<KT, T, MEAS>(a, u, slot, pre, acc, res);
       }
     }
   }
-  if (!a.resid) return;
+  if (!MEAS) return;
   __shared__ float sred[8][KT];
 #pragma unroll
   for (int off = L; off < 32; off <<= 1)
