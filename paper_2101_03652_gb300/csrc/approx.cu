@@ -488,9 +488,14 @@ static ppr_status run_approx(ppr_graph* g, const int32_t* src, int32_t k, const 
   const size_t cells = (size_t)n * KT;
   const int max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : 4096;
   const int32_t max_steps = 1 << 16;
-  const bool pi_host = !is_device_pointer(out_pi);
-  const bool r_host = out_r && !is_device_pointer(out_r);
-  const bool c_host = out_counts && !is_device_pointer(out_counts);
+  // outputs the kernels can write directly (device memory or pinned host
+  // memory); the rest is staged on the device and copied at the end
+  double* pi_view = static_cast<double*>(device_view(out_pi));
+  double* r_view = out_r ? static_cast<double*>(device_view(out_r)) : nullptr;
+  uint32_t* c_view = out_counts ? static_cast<uint32_t*>(device_view(out_counts)) : nullptr;
+  const bool pi_host = pi_view == nullptr;
+  const bool r_host = out_r && r_view == nullptr;
+  const bool c_host = out_counts && c_view == nullptr;
 
   ppr_graph::SweepPlan* plan = nullptr;
   PPR_TRY(get_plan(g, Lay32<KT>::L, &plan, st));
@@ -550,12 +555,12 @@ static ppr_status run_approx(ppr_graph* g, const int32_t* src, int32_t k, const 
   int32_t* d_src = ws.counters.as<int32_t>() + 1024;
   u64* hpin = static_cast<u64*>(ws.pinned);
   double* stage_p = ws.stage.as<double>();
-  double* pi_dev = pi_host ? stage_p : out_pi;
-  double* r_dev = !out_r ? nullptr : (r_host ? stage_p + (pi_host ? (size_t)k * n : 0) : out_r);
+  double* pi_dev = pi_host ? stage_p : pi_view;
+  double* r_dev = !out_r ? nullptr : (r_host ? stage_p + (pi_host ? (size_t)k * n : 0) : r_view);
   uint32_t* c_dev = !out_counts ? nullptr
                                 : (c_host ? reinterpret_cast<uint32_t*>(stage_p + (pi_host ? (size_t)k * n : 0) +
                                                                         (r_host ? (size_t)k * n : 0))
-                                          : out_counts);
+                                          : c_view);
   PPR_TRY(ensure_alpha(g, alpha, st));
   int bps = 0;
   PPR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, apx_sweep_kernel<KT>, 256, 0));

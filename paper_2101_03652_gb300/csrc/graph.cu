@@ -62,6 +62,21 @@ void Workspace::release() {
   pinned_bytes = 0;
 }
 
+// Address kernels can write an output through: device or managed memory as
+// is; page-locked host memory through its mapped device address (on a
+// Grace-Blackwell node the GPU writes it over the coherent CPU-GPU link, so
+// no staging copy is needed); NULL for pageable host memory, which is staged.
+void* device_view(void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
+  return nullptr;
+}
+
 bool is_device_pointer(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {

@@ -731,8 +731,12 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
   const double alpha = o.alpha, lambda = o.lambda;
   Workspace& ws = g->ws;
   const size_t cells = (size_t)n * KT;
-  const bool pi_on_host = !is_device_pointer(out_pi);
-  const bool r_on_host = out_r && !is_device_pointer(out_r);
+  // outputs the kernels can write directly (device memory or pinned host
+  // memory); the rest is staged on the device and copied at the end
+  double* pi_view = static_cast<double*>(device_view(out_pi));
+  double* r_view = out_r ? static_cast<double*>(device_view(out_r)) : nullptr;
+  const bool pi_on_host = pi_view == nullptr;
+  const bool r_on_host = out_r && r_view == nullptr;
   const int max_sweeps = o.max_sweeps > 0 ? o.max_sweeps
                                           : 4 * (int)std::ceil(std::log(lambda) / std::log(1.0 - alpha)) + 64;
 
@@ -798,8 +802,8 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
   u64* hpin = static_cast<u64*>(ws.pinned);
   int32_t* d_src = reinterpret_cast<int32_t*>(counters + 512);  // device copy of the tile's sources
   u64* mass = counters + 256;                                    // exact column sums of the output
-  double* out_pi_dev = pi_on_host ? ws.stage.as<double>() : out_pi;
-  double* out_r_dev = !out_r ? nullptr : (r_on_host ? ws.stage.as<double>() + (pi_on_host ? (size_t)k * n : 0) : out_r);
+  double* out_pi_dev = pi_on_host ? ws.stage.as<double>() : pi_view;
+  double* out_r_dev = !out_r ? nullptr : (r_on_host ? ws.stage.as<double>() + (pi_on_host ? (size_t)k * n : 0) : r_view);
 
   const u64 alpha64 = (u64)(alpha * 18446744073709551616.0);
   const u64 alpha_raw = (u64)(alpha * kFixOne);

@@ -384,3 +384,34 @@ def test_rmat22_hp_bench_configuration(P):
     og = O.Graph(rp, ci)
     ref, _, _ = O.powerpush(og, int(src[0]), ALPHA, LAM)
     assert np.abs(pi[0] - ref).sum() <= 2 * LAM
+
+
+def test_pinned_host_outputs_written_directly(P, c0, c0_ref):
+    """Page-locked host outputs are written by the kernels through their mapped
+    address (no staging); results equal those written to device buffers."""
+    rp, ci, src = c0
+    n = len(rp) - 1
+    g = P.Graph(rp, ci)
+    k = 4
+    host_pi = torch.empty((k, n), dtype=torch.float64, pin_memory=True)
+    host_r = torch.empty((k, n), dtype=torch.float64, pin_memory=True)
+    _, st = g.query(src[:k], P.PPR_HP, out_pi=host_pi, out_r=host_r, lam=LAM, k_tile=4, flags=P.PPR_FLAG_SYNC)
+    dev_pi, st_d = g.query(src[:k], P.PPR_HP, lam=LAM, k_tile=4, flags=P.PPR_FLAG_SYNC)
+    torch.cuda.synchronize()
+    assert np.array_equal(host_pi.numpy(), dev_pi.cpu().numpy())  # synchronous passes are deterministic
+    for i, s in enumerate(src[:k]):
+        assert np.abs(host_pi[i].numpy() - c0_ref[int(s)]).sum() <= 2 * LAM
+        assert np.abs(host_r[i].numpy()).sum() <= st[i]["final_l1_residual"]
+    apx_pi = torch.empty((k, n), dtype=torch.float64, pin_memory=True)
+    apx_c = torch.empty((k, n), dtype=torch.int32, pin_memory=True)
+    apx_r = torch.empty((k, n), dtype=torch.float64, pin_memory=True)
+    _, st_a = g.query(src[:k], P.PPR_APPROX, out_pi=apx_pi, out_r=apx_r, out_walk_counts=apx_c, eps=0.5, k_tile=4,
+                      seed=0x5EED)
+    torch.cuda.synchronize()
+    g.close()
+    og = O.Graph(rp, ci)
+    for i in range(k):
+        # the counts written to host memory replay bit for bit from the residue written beside them
+        oc, _, _ = O.walks(og, apx_r[i].numpy(), st_a[i]["W"], 0x5EED, i, ALPHA)
+        assert np.array_equal(apx_c[i].numpy().view(np.uint32), oc)
+        assert abs(apx_pi[i].numpy().sum() - 1.0) < 1e-4
