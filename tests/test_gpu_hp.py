@@ -415,3 +415,53 @@ def test_pinned_host_outputs_written_directly(P, c0, c0_ref):
         oc, _, _ = O.walks(og, apx_r[i].numpy(), st_a[i]["W"], 0x5EED, i, ALPHA)
         assert np.array_equal(apx_c[i].numpy().view(np.uint32), oc)
         assert abs(apx_pi[i].numpy().sum() - 1.0) < 1e-4
+
+
+def _random_tiny_graph(n, p, seed):
+    """Erdos-Renyi G(n, p) digraph, no self-loops, every sink given one random
+    out-edge (the library's graph contract)."""
+    rng = np.random.default_rng(seed)
+    a = rng.random((n, n)) < p
+    np.fill_diagonal(a, False)
+    for v in range(n):
+        if not a[v].any():
+            a[v, (v + 1 + rng.integers(n - 1)) % n] = True
+    edges = [(int(u), int(v)) for u, v in zip(*np.nonzero(a))]
+    return gen.from_edges(n, edges)
+
+
+@pytest.mark.parametrize("n,p,seed", [(2, 0.5, 1), (5, 0.3, 2), (17, 0.1, 3), (33, 0.05, 4), (64, 0.02, 5),
+                                      (64, 0.5, 6)])
+def test_random_tiny_graphs_every_mode(P, n, p, seed):
+    """Random graphs with n <= 64, every node as a source (one tile), every HP
+    mode, against a brute-force dense solve of Eq. 1."""
+    rp, ci = _random_tiny_graph(n, p, seed)
+    og = O.Graph(rp, ci)
+    exact = np.stack([O.dense_solve(og, s, ALPHA) for s in range(n)])
+    src = np.arange(n, dtype=np.int32)
+    modes = [{}, {"flags": P.PPR_FLAG_FIXED_PASSES}, {"flags": P.PPR_FLAG_SYNC}, {"switch_edges": 0},
+             {"epoch_num": 8, "flags": P.PPR_FLAG_NO_ACTIVE}, {"flags": P.PPR_FLAG_FP32_ONLY}]
+    for kw in modes:
+        pi, st = run(P, rp, ci, src, **kw)
+        check_bound_and_mass(st)
+        err = np.abs(pi - exact).sum(axis=1)
+        assert np.all(err <= LAM + 1e-12), (kw, err.max())
+
+
+@pytest.mark.parametrize("n,p,seed", [(17, 0.1, 3), (64, 0.02, 5)])
+def test_random_tiny_graphs_walk_counts(P, n, p, seed):
+    """SpeedPPR on random tiny graphs: walk counts bit-exact against the
+    oracle's replay from the residue the walks started from."""
+    rp, ci = _random_tiny_graph(n, p, seed)
+    og = O.Graph(rp, ci)
+    g = P.Graph(rp, ci)
+    src = np.arange(min(n, 16), dtype=np.int32)
+    out_r = torch.empty((len(src), n), dtype=torch.float64, device="cuda")
+    counts = torch.empty((len(src), n), dtype=torch.int32, device="cuda")
+    _, st = g.query(src, P.PPR_APPROX, out_r=out_r, out_walk_counts=counts, eps=0.5, seed=0x5EED)
+    torch.cuda.synchronize()
+    r, c = out_r.cpu().numpy(), counts.cpu().numpy().view(np.uint32)
+    g.close()
+    for i in range(len(src)):
+        oc, _, _ = O.walks(og, r[i], st[i]["W"], 0x5EED, i, ALPHA)
+        assert np.array_equal(c[i], oc)
