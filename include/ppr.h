@@ -81,15 +81,20 @@ typedef struct {
                               than this many out-edges over the tile; -1 = auto, 0 = no
                               queue phase (sweeps from the start) */
   int32_t max_sweeps;      /* bound on dense sweeps; 0 = 4*ceil(ln lambda/ln(1-alpha))+64 */
-  int32_t flags;           /* HP: PPR_FLAG_PARTIAL returns the estimate after exactly
-                              max_sweeps passes without certifying lambda (the stats'
-                              final_l1_residual is then the bound reached) */
+  int32_t flags;           /* OR of the PPR_FLAG_* bits above.  PPR_FLAG_PARTIAL (HP)
+                              returns the estimate after exactly max_sweeps passes
+                              without certifying lambda (the stats' final_l1_residual
+                              is then the bound reached) */
   const void* warm_start;  /* HP only: a ppr_model* of the same graph, or NULL for the
-                              zero start; the queue phase is skipped when set */
+                              zero start.  A model without correction passes supplies
+                              the start (the queue phase is skipped); a model with
+                              correction passes L adds its correction after the first
+                              L passes of the dense phase */
 } ppr_query_opts;
 
 typedef struct {
-  int32_t sweeps;              /* dense sweeps run for this source's tile */
+  int32_t sweeps;              /* dense passes run for this source's tile (correction and
+                                  exact passes together in the default HP mode) */
   int32_t levels;              /* frontier levels (queue phase) */
   int64_t edges_pushed;        /* out-edges scattered in the queue phase (this source) */
   int64_t edges_swept;         /* in-edges gathered by dense sweeps (m per sweep) */
@@ -97,7 +102,9 @@ typedef struct {
   int64_t walk_steps;          /* APPROX: total walk moves */
   double initial_l1_residual;  /* ||r||_1 when the dense phase started */
   double final_l1_residual;    /* certified bound on ||pi - pi_hat||_1 (HP) */
-  double mass_deficit;         /* 1 - sum(pi_hat); equals ||r||_1 for a zero start */
+  double mass_deficit;         /* 1 - sum(pi_hat) = sum(pi - pi_hat), so |mass_deficit| is at
+                                  most final_l1_residual (it equals ||r||_1 when the answer is
+                                  a push reserve, e.g. a queue-only or epoch query) */
   double ms_push;               /* device time of the queue phase (whole call) */
   double ms_sweep;              /* device time of the sweep kernels alone (whole call) */
   double ms_walk;               /* APPROX: device time of the walk phase */
