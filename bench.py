@@ -340,6 +340,7 @@ def run_gpu(args):
     achieved = per_launch / (avg_sweep_ms / 1e3) / 1e9
     peak, peak_kind = peaks()
     cpu = None
+    cpu_context = None
     if ws == 1 and not args.skip_cpu:
         import oracle as O
         og = O.Graph(rp, ci)
@@ -357,6 +358,21 @@ def run_gpu(args):
             alg = "Algorithm 4 with walks drawn per query (no index)"
         cpu = {"value": done / dt, "unit": "queries/s", "cores": 1, "kind": "oracle",
                "sample": f"{done} of the workload's sources, {alg} in FP64 on one host core"}
+        if not approx:
+            # context: the plain power iteration on all host cores (OpenMP)
+            from oracle import context as CX
+            cg = CX.ContextGraph(rp, ci)
+            t = time.perf_counter()
+            done_c = 0
+            while done_c < 1 or (time.perf_counter() - t < 5 and done_c < 8):
+                CX_pi, CX_it = cg.powitr(int(src[done_c]), ALPHA, LAMBDA)
+                done_c += 1
+            dt_c = time.perf_counter() - t
+            cg.close()
+            cpu_context = {"value": done_c / dt_c, "unit": "queries/s", "cores": CX.threads(),
+                           "kind": "powitr_openmp",
+                           "sample": f"{done_c} of the workload's sources, PowItr ({CX_it} iterations) in FP64 "
+                                     f"on {CX.threads()} host threads; context, not a baseline"}
     rec = {
         "metric": METRIC_APPROX if approx else METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -378,6 +394,7 @@ def run_gpu(args):
                      "algorithmic_bytes_per_launch": per_launch,
                      "avg_launch_ms": avg_sweep_ms},
         "cpu_baseline": cpu,
+        "cpu_context": cpu_context,
         "warm_start": warm,
         "gpu_launches": launches,
         "clocks": clk.summary(),
