@@ -42,6 +42,7 @@ WORKLOADS = {
 }
 APPROX_WORKLOADS = ("rmat22-approx", "rmat22-index")
 ALPHA, LAMBDA, EPS = 0.2, 1e-8, 0.5
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (the measured copy bandwidth is the roofline's peak)
 METRIC = "SSPPR queries/s at l1<=1e-8 (HP, plain GPU method)"
 METRIC_APPROX = "SSPPR queries/s, eps=0.5 relative error for pi>=1/n (SpeedPPR)"
 
@@ -390,6 +391,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": 8 * k * n},
         "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                      "traffic": None if approx else ncu_traffic(args.workload, kernel_name.split("<")[0]),
                      "algorithmic_bytes_per_launch": per_launch,
                      "avg_launch_ms": avg_sweep_ms},
