@@ -339,6 +339,8 @@ def run_gpu(args):
         per_launch = sweep_bytes(n, m, kt)
         kernel_name = f"sweep_kernel<{kt}>"
     achieved = per_launch / (avg_sweep_ms / 1e3) / 1e9
+    # DRAM bytes per launch from the committed ncu capture (None if the source changed since)
+    traffic = None if approx else ncu_traffic(args.workload, kernel_name.split("<")[0])
     peak, peak_kind = peaks()
     cpu = None
     cpu_context = None
@@ -392,7 +394,8 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
-                     "traffic": None if approx else ncu_traffic(args.workload, kernel_name.split("<")[0]),
+                     "traffic": traffic,
+                     "traffic_gbs": None if traffic is None else traffic / (avg_sweep_ms / 1e3) / 1e9,
                      "algorithmic_bytes_per_launch": per_launch,
                      "avg_launch_ms": avg_sweep_ms},
         "cpu_baseline": cpu,
