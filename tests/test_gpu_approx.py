@@ -42,7 +42,7 @@ def run_approx(P, rp, ci, src, eps=0.5, **kw):
     return res
 
 
-@pytest.mark.parametrize("k_tile", [1, 4, 16])
+@pytest.mark.parametrize("k_tile", [1, 2, 4, 8, 16, 32])
 def test_walk_counts_bit_exact(P, k_tile):
     rp, ci = gen.chung_lu(3000, 30000, 2.2, seed=5)
     og = O.Graph(rp, ci)

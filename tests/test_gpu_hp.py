@@ -465,3 +465,20 @@ def test_random_tiny_graphs_walk_counts(P, n, p, seed):
     for i in range(len(src)):
         oc, _, _ = O.walks(og, r[i], st[i]["W"], 0x5EED, i, ALPHA)
         assert np.array_equal(c[i], oc)
+
+
+def test_many_sources_two_tiles(P, c0):
+    """100 sources (duplicates included) in 64-column tiles: two tiles, the
+    second ragged; every answer against the oracle."""
+    rp, ci, _ = c0
+    og = O.Graph(rp, ci)
+    src = gen.sources(len(rp) - 1, 96, seed=12)
+    src = np.concatenate([src, src[:4]]).astype(np.int32)
+    pi, st = run(P, rp, ci, src)
+    check_bound_and_mass(st)
+    refs = {}
+    for i, s in enumerate(src):
+        if int(s) not in refs:
+            refs[int(s)] = O.powerpush(og, int(s), ALPHA, LAM)[0]
+        assert np.abs(pi[i] - refs[int(s)]).sum() <= 2 * LAM, i
+    assert np.abs(pi[96:] - pi[:4]).sum(axis=1).max() <= 2 * LAM  # duplicates agree

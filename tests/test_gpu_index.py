@@ -55,7 +55,7 @@ def test_index_endpoints_bit_exact(P, chung_lu, graph):
     g.close()
 
 
-@pytest.mark.parametrize("k_tile", [1, 8])
+@pytest.mark.parametrize("k_tile", [1, 8, 16, 32])
 def test_index_query_counts_bit_exact(P, chung_lu, k_tile):
     rp, ci = chung_lu
     og = O.Graph(rp, ci)
