@@ -121,6 +121,7 @@ TRAFFIC_FILES = {
     # kernel family: (committed ncu summary, sources the capture was taken on)
     "sweep_kernel": ("sweep_kernel_traffic.json", ("sweep_kernel.cuh",)),
     "refine_pass_kernel": ("refine_pass_kernel_traffic.json", ("refine_kernel.cuh", "f32_lanes.cuh", "sweep_kernel.cuh")),
+    "walk_kernel": ("walk_kernel_traffic.json", ("walk_kernel.cuh",)),
 }
 
 
@@ -135,6 +136,8 @@ def kernel_source_sha(sources=("sweep_kernel.cuh",)) -> str:
 def ncu_traffic(workload: str, kernel: str = "sweep_kernel"):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source."""
+    if kernel not in TRAFFIC_FILES:
+        return None
     fname, sources = TRAFFIC_FILES[kernel]
     path = os.path.join(ROOT, "profiles", fname)
     try:
@@ -340,7 +343,7 @@ def run_gpu(args):
         kernel_name = f"sweep_kernel<{kt}>"
     achieved = per_launch / (avg_sweep_ms / 1e3) / 1e9
     # DRAM bytes per launch from the committed ncu capture (None if the source changed since)
-    traffic = None if approx else ncu_traffic(args.workload, kernel_name.split("<")[0])
+    traffic = ncu_traffic(args.workload, kernel_name.split("<")[0])
     peak, peak_kind = peaks()
     cpu = None
     cpu_context = None
