@@ -101,3 +101,16 @@ def test_stats_layout_matches_the_header():
     body = re.search(r"typedef struct \{([^}]*)\} ppr_stats;", text, flags=re.S).group(1)
     fields = re.findall(r"\b(?:int32_t|int64_t|double)\s+([A-Za-z_0-9]+)\s*;", body)
     assert [f for f, _ in binding.ppr_stats._fields_] == fields
+
+
+@pytest.mark.parametrize("n,m", [(5, 1 << 31), (1 << 31, 1 << 31), (5, 4)])
+def test_size_limits_rejected_before_reading(n, m):
+    """n <= m < 2^31 (int32 ids and edge offsets); the sizes are checked before
+    either array is read, so small arrays with out-of-range sizes are safe."""
+    lib = P.load_library()
+    rp, ci = gen.fig1_graph()
+    h = ctypes.c_void_p()
+    st = lib.ppr_graph_load(rp.ctypes.data_as(ctypes.c_void_p), ci.ctypes.data_as(ctypes.c_void_p),
+                            ctypes.c_int64(n), ctypes.c_int64(m), None, ctypes.byref(h))
+    assert st == binding.PPR_ERR_GRAPH and not h.value
+    assert b"2^31" in lib.ppr_last_error()
