@@ -166,6 +166,9 @@ def test_argument_errors(P, c0):
     for bad in ([-1], [10_000]):
         with pytest.raises(P.PPRError):
             g.query(bad, P.PPR_HP)
+    for mode in (P.PPR_HP, P.PPR_APPROX):  # an empty source list is an argument error
+        with pytest.raises(P.PPRError):
+            g.query(np.zeros(0, dtype=np.int32), mode)
     for kw in ({"lam": 0.0}, {"alpha": 1.0}, {"alpha": 0.0}, {"k_tile": 3}, {"max_sweeps": 5}):
         with pytest.raises(P.PPRError):
             g.query(src[:2], P.PPR_HP, **kw)
@@ -482,3 +485,31 @@ def test_many_sources_two_tiles(P, c0):
             refs[int(s)] = O.powerpush(og, int(s), ALPHA, LAM)[0]
         assert np.abs(pi[i] - refs[int(s)]).sum() <= 2 * LAM, i
     assert np.abs(pi[96:] - pi[:4]).sum(axis=1).max() <= 2 * LAM  # duplicates agree
+
+
+def test_rmat25_serving_configuration(P):
+    """R-MAT scale 25, edge factor 32 (n = 33.6 M, m = 1.06 G): one batch of 32
+    sources as the serving workload launches it.  No full oracle solve fits
+    this size, so every source is checked by its certified bound and the mass
+    identity, and two sampled sources by the push residual of the returned
+    pi_hat evaluated by the oracle in FP64: ||pi - pi_hat||_1 <= ||r||_1."""
+    rp, ci = gen.rmat(25, 32, seed=1)
+    n = len(rp) - 1
+    src = gen.sources(n, 32, seed=6)
+    g = P.Graph(rp, ci)
+    pi_d, st = g.query(src, P.PPR_HP, lam=LAM)
+    torch.cuda.synchronize()
+    check_bound_and_mass(st)
+    og = O.Graph(rp, ci)
+    d_in_max = int(np.bincount(ci, minlength=n).max())
+    for i in (0, 17):
+        x = pi_d[i].cpu().numpy()
+        assert x.min() >= 0
+        r = O.residual(og, int(src[i]), x, ALPHA)
+        # FP64 evaluation: node u sums d_in(u) shares plus a few rounded steps,
+        # each error at most 2^-53 of the magnitudes summed (2 sum x + alpha in all)
+        slack = (d_in_max + 5) * 2.0**-53 * (2 * x.sum() + ALPHA) / ALPHA
+        assert slack < LAM / 10
+        assert np.abs(r).sum() <= st[i]["final_l1_residual"] + slack <= LAM + slack
+        assert abs(r.sum() - st[i]["mass_deficit"]) <= 1e-12 + slack
+    g.close()
