@@ -117,6 +117,13 @@ def fp32_pass_bytes(n: int, m: int, kt: int) -> int:
     return 4 * (n + 1) + 4 * m + 4 * n + 16 * n * kt
 
 
+def fp32_pass_bytes_min(n: int, m: int, kt: int) -> int:
+    """Lower bound of the same pass under an ideal cache: z_e read once in all
+    (the own old row coming from the gathered copy), written once, r_f read
+    once (12 n kt)."""
+    return 4 * (n + 1) + 4 * m + 4 * n + 12 * n * kt
+
+
 TRAFFIC_FILES = {
     # kernel family: (committed ncu summary, sources the capture was taken on)
     "sweep_kernel": ("sweep_kernel_traffic.json", ("sweep_kernel.cuh",)),
@@ -341,7 +348,10 @@ def run_gpu(args):
         avg_sweep_ms = sweep_ms / max(sweep_launches, 1)
         per_launch = sweep_bytes(n, m, kt)
         kernel_name = f"sweep_kernel<{kt}>"
+    # the other kernels' counts are already their minimum
+    per_launch_min = fp32_pass_bytes_min(n, m, kt) if kernel_name.startswith("refine_pass_kernel") else per_launch
     achieved = per_launch / (avg_sweep_ms / 1e3) / 1e9
+    achieved_min = per_launch_min / (avg_sweep_ms / 1e3) / 1e9
     # DRAM bytes per launch from the committed ncu capture (None if the source changed since)
     traffic = ncu_traffic(args.workload, kernel_name.split("<")[0])
     peak, peak_kind = peaks()
@@ -400,6 +410,8 @@ def run_gpu(args):
                      "traffic": traffic,
                      "traffic_gbs": None if traffic is None else traffic / (avg_sweep_ms / 1e3) / 1e9,
                      "algorithmic_bytes_per_launch": per_launch,
+                     "algorithmic_bytes_lower_bound": per_launch_min,
+                     "frac_of_lower_bound": achieved_min / peak,
                      "avg_launch_ms": avg_sweep_ms},
         "cpu_baseline": cpu,
         "cpu_context": cpu_context,
