@@ -4,6 +4,10 @@ Plain, single-threaded C (ppr_oracle.c) with a thin ctypes wrapper.  Only the
 tests, the smoke check and the benchmark's CPU-baseline leg use this package;
 the CUDA library never imports or links it, and it imports nothing from the
 CUDA library.  Each function names the passage of arXiv 2101.03652 it follows.
+
+ORACLE_LIBRARY, when set, names a build to load instead of liboracle.so: the
+test that plants mistakes in copies of ppr_oracle.c uses it to check that the
+pins catch each one.
 """
 from __future__ import annotations
 
@@ -61,7 +65,7 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
+            lib = ctypes.CDLL(os.environ.get("ORACLE_LIBRARY") or build())
             P = ctypes.c_void_p
             I64, I32, U32, U64, D = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
             S = ctypes.POINTER(Stats)

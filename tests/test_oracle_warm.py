@@ -79,3 +79,33 @@ def test_zero_basis_returns_sketch():
     h = np.ones((2, 4))
     X, _ = Wm.basis_forward(S, np.zeros((g.n, 4)), h)
     np.testing.assert_allclose(X, S, atol=1e-15)
+
+
+def test_gelu_at_standard_normal_table_values():
+    """GELU(x) = x Phi(x) (erf form); Phi(1) and Phi(2) from a standard normal
+    table, and the derivative Phi(x) + x phi(x) at 0 and 1 (phi(1) = 0.2419707245)."""
+    x = np.array([0.0, 1.0, -1.0, 2.0])
+    np.testing.assert_allclose(Wm.gelu(x), [0.0, 0.8413447461, -0.1586552539, 2 * 0.9772498681], atol=1e-9)
+    np.testing.assert_allclose(Wm.gelu_grad(np.array([0.0, 1.0])), [0.5, 0.8413447461 + 0.2419707245], atol=1e-9)
+
+
+def test_bf16_rounding_matches_torch():
+    """Round to nearest, ties to even: torch's float32 -> bfloat16 conversion."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(1)
+    x = np.concatenate([rng.normal(0, 1, 4000), rng.normal(0, 1e-6, 1000)]).astype(np.float32)
+    # exact halfway cases around 1 and 2^-100 (both even and odd lower neighbours)
+    hi = np.concatenate([0x3F80 + np.arange(64), 0x0D80 + np.arange(64)]).astype(np.uint32)
+    ties = (hi << 16 | 0x8000).view(np.float32)
+    x = np.concatenate([x, ties, -ties])
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(Wm.bf16(x), ref)
+
+
+def test_features_equal_dense_product():
+    """f = S^T G, brute force with every row of G drawn (the oracle skips the
+    rows where S is zero)."""
+    g = small_graph()
+    S = Wm.sketches(g, [0, 9, 31], ALPHA)
+    G = O.gaussian_rows(0, g.n, 16, seed=5)
+    np.testing.assert_allclose(Wm.features(S, 16, seed=5), S.T @ G, rtol=1e-12, atol=1e-14)
