@@ -221,8 +221,13 @@ ppr_status ppr_autotune(ppr_graph* g, const int32_t* src, int32_t k, const ppr_q
  * ppr_sssp_query(..., PPR_APPROX) with flags PPR_FLAG_INDEX then reads, for
  * each v with r(v) > 0, the first W_v = min(ceil(r(v) W), d_v) stored
  * endpoints of v instead of walking.  Builds on the device (4 m bytes, kept
- * with the graph).  ppr_index_get copies the endpoints to a host int32[m] in
- * the caller's slot order and node ids.
+ * with the graph; a rebuild replaces it).  ppr_index_get copies the endpoints
+ * to a host int32[m] in the caller's slot order and node ids; it blocks.
+ * Errors: PPR_ERR_ARG (NULL graph or output, alpha outside (0, 1), or
+ * ppr_index_get before any build), PPR_ERR_OOM (no room for the 4 m bytes),
+ * PPR_ERR_NOT_CONVERGED (a stored walk longer than 2^16 steps), PPR_ERR_CUDA.
+ * An indexed query on a graph without an index, or with one built for another
+ * alpha, fails with PPR_ERR_ARG.
  */
 ppr_status ppr_index_build(ppr_graph* g, uint64_t seed, double alpha, void* cuda_stream);
 ppr_status ppr_index_get(const ppr_graph* g, int32_t* endpoints);
@@ -233,7 +238,7 @@ void ppr_free(ppr_graph* g);
 /* Message of the last error on the calling thread ("" if none). */
 const char* ppr_last_error(void);
 
-/* Graph sizes: n, m as loaded. */
+/* Graph sizes: n, m as loaded (0 for a NULL graph). */
 int64_t ppr_graph_n(const ppr_graph* g);
 int64_t ppr_graph_m(const ppr_graph* g);
 
@@ -282,21 +287,32 @@ ppr_status ppr_model_train(ppr_model* model, const int32_t* train_src, int32_t n
 
 /* One forward/backward over k <= 64 sources with labels (k x n float64, host
  * or device, caller's node order); lr > 0 also applies one Adam step.  loss
- * receives the mean l1 error of the batch. */
+ * receives the mean l1 error of the batch.  Errors: PPR_ERR_ARG (NULL model
+ * or labels, k outside 1..64, lr < 0, a source out of range), PPR_ERR_OOM,
+ * PPR_ERR_CUDA. */
 ppr_status ppr_model_train_step(ppr_model* model, const int32_t* src, int32_t k, const double* labels, float lr,
                                 double* loss, void* cuda_stream);
 
-/* The model's estimate x for k sources (k x n float64, host or device). */
+/* The model's estimate x for k sources (k x n float64, host or device).
+ * Errors: PPR_ERR_ARG (NULL model or output, k < 1, a source out of range),
+ * PPR_ERR_OOM, PPR_ERR_CUDA. */
 ppr_status ppr_model_estimate(ppr_model* model, const int32_t* src, int32_t k, double* out_x, void* cuda_stream);
 
-/* Parameters and last gradients, flat float32 in the order W1 (feat x hidden),
- * b1, W2 (hidden x hidden), b2, W3 (hidden x rank), b3, U (n x rank, caller's
- * node order); either pointer may be NULL. */
+/* Parameters and last gradients, flat float32 host arrays of
+ * ppr_model_param_count entries (0 for a NULL model) in the order W1
+ * (feat x hidden), b1, W2 (hidden x hidden), b2, W3 (hidden x rank), b3,
+ * U (n x rank, caller's node order); either pointer of get_params may be
+ * NULL.  set_params also refreshes the BF16 copies.  Errors: PPR_ERR_ARG
+ * (NULL model, or NULL params for set_params), PPR_ERR_CUDA. */
 int64_t ppr_model_param_count(const ppr_model* model);
 ppr_status ppr_model_get_params(const ppr_model* model, float* params, float* grads);
 ppr_status ppr_model_set_params(ppr_model* model, const float* params);
 
-/* Checkpoint (parameters and Adam moments) to a binary file, and back. */
+/* Checkpoint (parameters and Adam moments) to a binary file, and back; a
+ * checkpoint loads only into a graph of the same n.  Errors: PPR_ERR_ARG
+ * (NULL arguments, a file that cannot be opened, read or recognised as a
+ * checkpoint for this graph), PPR_ERR_CUDA (save: a copy or write failed),
+ * PPR_ERR_OOM (load).  ppr_model_free accepts NULL. */
 ppr_status ppr_model_save(const ppr_model* model, const char* path);
 ppr_status ppr_model_load(ppr_graph* g, const char* path, ppr_model** out);
 void ppr_model_free(ppr_model* model);
