@@ -310,9 +310,10 @@ ppr_status ppr_model_set_params(ppr_model* model, const float* params);
 
 /* Checkpoint (parameters and Adam moments) to a binary file, and back; a
  * checkpoint loads only into a graph of the same n.  Errors: PPR_ERR_ARG
- * (NULL arguments, a file that cannot be opened, read or recognised as a
- * checkpoint for this graph), PPR_ERR_CUDA (save: a copy or write failed),
- * PPR_ERR_OOM (load).  ppr_model_free accepts NULL. */
+ * (NULL arguments, a file that cannot be opened, written, read or
+ * recognised as a checkpoint for this graph), PPR_ERR_CUDA (save: a copy
+ * from the device failed), PPR_ERR_OOM (load).  ppr_model_free accepts
+ * NULL. */
 ppr_status ppr_model_save(const ppr_model* model, const char* path);
 ppr_status ppr_model_load(ppr_graph* g, const char* path, ppr_model** out);
 void ppr_model_free(ppr_model* model);

@@ -1115,14 +1115,15 @@ ppr_status ppr_model_save(const ppr_model* md, const char* path) {
   if (!fp) { set_error("cannot open %s for writing", path); return PPR_ERR_ARG; }
   const int64_t hdr[9] = {0x4d525050, 2, md->g->n, md->F, md->H, md->R, (int64_t)md->seed, md->step, md->L};
   std::vector<float> buf(md->n_params);
-  bool ok = fwrite(hdr, sizeof(hdr), 1, fp) == 1;
+  bool io_ok = fwrite(hdr, sizeof(hdr), 1, fp) == 1, cuda_ok = true;
   for (const float* src : {md->p, md->m, md->v}) {
-    if (!ok) break;
-    ok = cudaMemcpy(buf.data(), src, sizeof(float) * md->n_params, cudaMemcpyDeviceToHost) == cudaSuccess &&
-         fwrite(buf.data(), sizeof(float), md->n_params, fp) == (size_t)md->n_params;
+    if (!io_ok) break;
+    cuda_ok = cudaMemcpy(buf.data(), src, sizeof(float) * md->n_params, cudaMemcpyDeviceToHost) == cudaSuccess;
+    io_ok = cuda_ok && fwrite(buf.data(), sizeof(float), md->n_params, fp) == (size_t)md->n_params;
   }
-  ok = (fclose(fp) == 0) && ok;
-  if (!ok) { set_error("writing %s failed", path); return PPR_ERR_CUDA; }
+  io_ok = (fclose(fp) == 0) && io_ok;
+  if (!cuda_ok) { set_error("copying the model from the device failed"); return PPR_ERR_CUDA; }
+  if (!io_ok) { set_error("writing %s failed", path); return PPR_ERR_ARG; }
   return PPR_OK;
 }
 

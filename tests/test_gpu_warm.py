@@ -146,6 +146,13 @@ def test_checkpoint_round_trip(P, setup):
         # evaluations of one model agree to FP32 rounding, not bit for bit
         np.testing.assert_allclose(m.estimate(src), m2.estimate(src), rtol=1e-5, atol=1e-9)
         m2.close()
+        with pytest.raises(P.PPRError) as e:      # not a checkpoint
+            P.Model.load(g, os.path.join(td, "missing.bin"))
+        assert e.value.status == P.binding.PPR_ERR_ARG
+    if os.path.exists("/dev/full"):               # a write that fails: ENOSPC
+        with pytest.raises(P.PPRError) as e:
+            m.save("/dev/full")
+        assert e.value.status == P.binding.PPR_ERR_ARG
     m.close()
 
 
