@@ -1,0 +1,49 @@
+"""Host logic of bench.py that its JSON line rests on (no GPU): the
+algorithmic byte counts of the dominant kernels, the measured peak, and the
+rule that an ncu traffic record is used only while the kernel's source is
+the one it was captured on."""
+import json
+
+import pytest
+
+import bench
+
+N20, M20 = 1_048_576, 16_586_703      # R-MAT scale 20, edge factor 16, seed 1, after cleaning
+
+
+def test_fp32_pass_bytes():
+    # in-CSR 4(n+1) + 4m, degrees 4n, then per node and column: z_e gathered,
+    # own old row, z_e written, r_f read (16 B) or, at the ideal-cache minimum, 12 B
+    base = 4 * (N20 + 1) + 4 * M20 + 4 * N20
+    assert bench.fp32_pass_bytes(N20, M20, 64) == base + 16 * N20 * 64
+    assert bench.fp32_pass_bytes_min(N20, M20, 64) == base + 12 * N20 * 64
+    assert round(bench.fp32_pass_bytes(N20, M20, 64) / 1e6, 1) == 1148.5
+    assert round(bench.fp32_pass_bytes_min(N20, M20, 64) / 1e6) == 880
+
+
+def test_sweep_bytes():
+    # in-CSR, per-node scales (12 B), the Q1.63 tile read and written once
+    assert bench.sweep_bytes(N20, M20, 64) == 4 * (N20 + 1) + 4 * M20 + 12 * N20 + 16 * N20 * 64
+    assert round(bench.sweep_bytes(N20, M20, 64) / 1e6, 1) == 1156.9
+
+
+def test_peak_is_the_measured_copy_bandwidth():
+    peak, kind = bench.peaks()
+    with open(bench.os.path.join(bench.ROOT, "MEASURED_PEAKS.json")) as f:
+        assert peak == float(json.load(f)["hbm_gbs"]) and kind == "measured"
+
+
+@pytest.mark.parametrize("kernel,workload", [("refine_pass_kernel", "rmat20-k64"), ("walk_kernel", "rmat22-approx")])
+def test_traffic_record_follows_the_kernel_source(monkeypatch, kernel, workload):
+    fname, sources = bench.TRAFFIC_FILES[kernel]
+    with open(bench.os.path.join(bench.ROOT, "profiles", fname)) as f:
+        rec = json.load(f)
+    assert rec["kernel_source_sha"] == bench.kernel_source_sha(sources), "record older than the kernel source"
+    assert bench.ncu_traffic(workload, kernel) == float(rec["dram_bytes_per_launch"])
+    assert bench.ncu_traffic("rmat22-k1", kernel) is None           # captured on another workload
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda sources=(): "0" * 16)
+    assert bench.ncu_traffic(workload, kernel) is None              # the kernel changed since the capture
+
+
+def test_unknown_kernel_has_no_traffic():
+    assert bench.ncu_traffic("rmat22-index", "index_query_kernel") is None
