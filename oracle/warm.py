@@ -138,6 +138,19 @@ def backward(params, S, f, pi, rnd=None):
     return L, [dW1, db1, dW2, db2, dW3, db3, dU]
 
 
+def adam_step(p, m, v, g, lr: float, t: int, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
+    """One Adam update (Kingma & Ba, ICLR 2015, Algorithm 1) at step t >= 1:
+    exponential moving averages of the gradient and of its square, each
+    divided by one minus its decay rate to the power t (bias correction), and
+    a step of lr times the corrected mean over the root of the corrected
+    second moment plus eps.  Returns (p, m, v)."""
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    m_hat = m / (1.0 - b1 ** t)
+    v_hat = v / (1.0 - b2 ** t)
+    return p - lr * m_hat / (np.sqrt(v_hat) + eps), m, v
+
+
 def warm_estimate(g: Graph, src, params, F: int, seed: int, alpha: float = 0.2, rnd=None) -> np.ndarray:
     """X for a batch of sources (n x B)."""
     S = sketches(g, src, alpha)

@@ -106,6 +106,29 @@ def test_gradients_match_oracle(P, setup):
     m.close()
 
 
+def test_adam_step_matches_oracle(P, setup):
+    """One training step of a fresh model (Adam step 1, zero moments): the
+    parameters move as the oracle's Adam step predicts from the gradients the
+    step computed.  The kernel works in FP32, with the decay rates rounded to
+    FP32 (up to 5e-5 relative in a bias correction); the steps are compared
+    within 1e-4 of lr, plus the rounding of the FP32 parameter."""
+    rp, ci, g, og = setup
+    rng = np.random.default_rng(4)
+    m = P.Model(g, seed=SEED)
+    randomize(m, og.n, rng)
+    p0 = m.get_params().astype(np.float64)
+    src = gen.sources(og.n, 8, seed=25)
+    labels = np.stack([O.powerpush(og, int(s), ALPHA, 1e-10)[0] for s in src])
+    lr = 1e-3
+    m.train_step(src, labels, lr=lr)
+    p1, grads = m.get_params(grads=True)
+    zero = np.zeros_like(p0)
+    ref, _, _ = Wm.adam_step(p0, zero, zero, grads.astype(np.float64), lr=lr, t=1)
+    assert np.abs(p1 - p0).max() > 0.5 * lr       # the step was taken
+    np.testing.assert_allclose(p1, ref, rtol=2.0**-23, atol=1e-4 * lr)
+    m.close()
+
+
 def test_training_reduces_loss_and_warm_query_is_exact(P, setup):
     rp, ci, g, og = setup
     n = og.n

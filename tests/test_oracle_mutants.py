@@ -127,6 +127,24 @@ def _backward_wrong_dU(params, S, f, pi, rnd=None):
     return L, g
 
 
+def _adam_without_bias_correction(p, m, v, g, lr, t, b1=0.9, b2=0.999, eps=1e-8):
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    return p - lr * m / (np.sqrt(v) + eps), m, v
+
+
+def _adam_decays_swapped(p, m, v, g, lr, t, b1=0.9, b2=0.999, eps=1e-8):
+    return _adam_step(p, m, v, g, lr, t, b1=b2, b2=b1, eps=eps)
+
+
+def _adam_without_root(p, m, v, g, lr, t, b1=0.9, b2=0.999, eps=1e-8):
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    return p - lr * (m / (1.0 - b1 ** t)) / (v / (1.0 - b2 ** t) + eps), m, v
+
+
+_adam_step = Wm.adam_step
+
 PY_MUTANTS = [
     ("gelu_grad_drops_term", "gelu_grad", _wrong_gelu_grad),
     ("gelu_tanh_form", "gelu", _tanh_gelu),
@@ -136,6 +154,9 @@ PY_MUTANTS = [
     ("features_row_off_by_one", "features", _features_off_by_one),
     ("basis_without_relu", "basis_forward", _basis_without_relu),
     ("backward_dU_sign", "backward", _backward_wrong_dU),
+    ("adam_without_bias_correction", "adam_step", _adam_without_bias_correction),
+    ("adam_decays_swapped", "adam_step", _adam_decays_swapped),
+    ("adam_without_root", "adam_step", _adam_without_root),
 ]
 
 

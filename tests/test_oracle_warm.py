@@ -109,3 +109,23 @@ def test_features_equal_dense_product():
     S = Wm.sketches(g, [0, 9, 31], ALPHA)
     G = O.gaussian_rows(0, g.n, 16, seed=5)
     np.testing.assert_allclose(Wm.features(S, 16, seed=5), S.T @ G, rtol=1e-12, atol=1e-14)
+
+
+def test_adam_step_closed_forms():
+    """Adam (Kingma & Ba, 2015): with bias correction the first step has size lr
+    in every coordinate whatever the gradient's scale, a constant gradient keeps
+    that size at every step, and a zero gradient moves nothing.  Gradients +1
+    then -1 give, by hand from the algorithm, -lr then +lr/19: in all
+    -(18/19) lr."""
+    g = np.array([3.0, -1e-3, 250.0, 0.0])
+    z = np.zeros(4)
+    p1, m1, v1 = Wm.adam_step(z, z, z, g, lr=1e-2, t=1)
+    np.testing.assert_allclose(p1, -1e-2 * np.sign(g), rtol=1e-5)
+    p, m, v = z, z, z
+    for t in range(1, 51):
+        p, m, v = Wm.adam_step(p, m, v, g, lr=1e-2, t=t)
+    np.testing.assert_allclose(p, -0.5 * np.sign(g), rtol=1e-5)
+    one = np.ones(1)
+    p, m, v = Wm.adam_step(np.zeros(1), np.zeros(1), np.zeros(1), one, lr=1.0, t=1)
+    p, m, v = Wm.adam_step(p, m, v, -one, lr=1.0, t=2)
+    np.testing.assert_allclose(p, -18.0 / 19.0, rtol=1e-6)
