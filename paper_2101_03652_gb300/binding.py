@@ -175,6 +175,35 @@ def _ptr(x):
     return x.data_ptr()
 
 
+def _buf(x, k: int, n: int, kind: str, name: str):
+    """Address of a k x n row-major buffer (numpy array or torch tensor, host
+    or device) that the library reads or writes through a raw pointer, checked
+    first: element type (kind "f64" = float64, "u32" = 32-bit counts),
+    contiguity, and room for k x n elements with rows of n."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if kind == "f64":
+            ok = x.dtype == np.float64
+        else:
+            ok = x.dtype in (np.int32, np.uint32)
+        contiguous, size, shape, addr = x.flags["C_CONTIGUOUS"], x.size, x.shape, x.ctypes.data
+    else:
+        import torch
+        if kind == "f64":
+            ok = x.dtype == torch.float64
+        else:
+            ok = x.dtype in (torch.int32, getattr(torch, "uint32", torch.int32))
+        contiguous, size, shape, addr = x.is_contiguous(), x.numel(), tuple(x.shape), x.data_ptr()
+    if not ok:
+        raise TypeError(f"{name}: needs {'float64' if kind == 'f64' else 'int32 or uint32'} elements, got {x.dtype}")
+    if not contiguous:
+        raise ValueError(f"{name}: must be contiguous (row-major)")
+    if size < k * n or (len(shape) >= 2 and shape[-1] != n):
+        raise ValueError(f"{name}: needs shape ({k}, {n}), got {tuple(shape)}")
+    return addr
+
+
 def _stream(stream):
     if stream is not None:
         return stream
@@ -201,9 +230,12 @@ def ppr_sssp_query(graph: int, src, mode: int, opts: ppr_query_opts, out_pi, out
                    stats: bool = True, stream=None):
     """Run k queries; out_* are torch tensors (CUDA or CPU) or numpy arrays of shape (k, n)."""
     s = np.ascontiguousarray(src, dtype=np.int32)
+    k, n = len(s), load_library().ppr_graph_n(graph)
     st = (ppr_stats * len(s))() if stats else None
-    _check(load_library().ppr_sssp_query(graph, s.ctypes.data, len(s), mode, ctypes.byref(opts), _ptr(out_pi),
-                                         _ptr(out_r), _ptr(out_walk_counts), st, _stream(stream)))
+    _check(load_library().ppr_sssp_query(graph, s.ctypes.data, len(s), mode, ctypes.byref(opts),
+                                         _buf(out_pi, k, n, "f64", "out_pi"), _buf(out_r, k, n, "f64", "out_r"),
+                                         _buf(out_walk_counts, k, n, "u32", "out_walk_counts"), st,
+                                         _stream(stream)))
     return [x.as_dict() for x in st] if stats else None
 
 
@@ -213,7 +245,8 @@ def ppr_sssp_query_noalloc(graph: int, src, out_pi, alpha: float = 0.2, lam: flo
     tensor.  Returns the passes run per source."""
     s = np.ascontiguousarray(src, dtype=np.int32)
     sweeps = np.zeros(len(s), dtype=np.int32)
-    _check(load_library().ppr_sssp_query_noalloc(graph, s.ctypes.data, len(s), alpha, lam, _ptr(out_pi),
+    out = _buf(out_pi, len(s), load_library().ppr_graph_n(graph), "f64", "out_pi")
+    _check(load_library().ppr_sssp_query_noalloc(graph, s.ctypes.data, len(s), alpha, lam, out,
                                                  sweeps.ctypes.data, _stream(stream)))
     return sweeps
 
@@ -333,7 +366,8 @@ class Model:
     def train_step(self, src, labels, lr: float = 0.0, stream=None) -> float:
         s = np.ascontiguousarray(src, dtype=np.int32)
         loss = ctypes.c_double()
-        _check(load_library().ppr_model_train_step(self.handle, s.ctypes.data, len(s), _ptr(labels), lr,
+        _check(load_library().ppr_model_train_step(self.handle, s.ctypes.data, len(s),
+                                                   _buf(labels, len(s), self.graph.n, "f64", "labels"), lr,
                                                    ctypes.byref(loss), _stream(stream)))
         return loss.value
 
@@ -341,7 +375,8 @@ class Model:
         s = np.ascontiguousarray(src, dtype=np.int32)
         if out is None:
             out = np.zeros((len(s), self.graph.n))
-        _check(load_library().ppr_model_estimate(self.handle, s.ctypes.data, len(s), _ptr(out), _stream(stream)))
+        _check(load_library().ppr_model_estimate(self.handle, s.ctypes.data, len(s),
+                                                 _buf(out, len(s), self.graph.n, "f64", "out"), _stream(stream)))
         return out
 
     def param_count(self) -> int:

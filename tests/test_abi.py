@@ -114,3 +114,102 @@ def test_size_limits_rejected_before_reading(n, m):
                             ctypes.c_int64(n), ctypes.c_int64(m), None, ctypes.byref(h))
     assert st == binding.PPR_ERR_GRAPH and not h.value
     assert b"2^31" in lib.ppr_last_error()
+
+
+def test_buffers_are_checked_before_the_library_writes_through_them():
+    """Output and label buffers reach the library as raw pointers; the binding
+    checks element type, contiguity and size first, so a wrong buffer is a
+    Python error instead of an out-of-bounds write on the device."""
+    torch = pytest.importorskip("torch")
+    k, n = 3, 7
+    ok = np.zeros((k, n))
+    assert binding._buf(ok, k, n, "f64", "out_pi") == ok.ctypes.data
+    assert binding._buf(None, k, n, "f64", "out_r") is None
+    assert binding._buf(np.zeros((k, n), dtype=np.uint32), k, n, "u32", "c") is not None
+    assert binding._buf(torch.zeros((k, n), dtype=torch.int32), k, n, "u32", "c") is not None
+    assert binding._buf(torch.zeros((k + 2, n), dtype=torch.float64), k, n, "f64", "out_pi") is not None
+    with pytest.raises(TypeError):
+        binding._buf(np.zeros((k, n), dtype=np.float32), k, n, "f64", "out_pi")
+    with pytest.raises(TypeError):
+        binding._buf(torch.zeros((k, n), dtype=torch.float32), k, n, "f64", "out_pi")
+    with pytest.raises(TypeError):
+        binding._buf(np.zeros((k, n)), k, n, "u32", "out_walk_counts")
+    with pytest.raises(ValueError):
+        binding._buf(np.zeros((k - 1, n)), k, n, "f64", "out_pi")          # too few rows
+    with pytest.raises(ValueError):
+        binding._buf(np.zeros((k, n + 1)), k, n, "f64", "out_pi")          # rows of the wrong length
+    with pytest.raises(ValueError):
+        binding._buf(np.zeros((n, k)).T, k, n, "f64", "out_pi")            # column-major
+    with pytest.raises(ValueError):
+        binding._buf(torch.zeros((k, 2 * n), dtype=torch.float64)[:, ::2], k, n, "f64", "out_pi")
+
+
+class _RecordingLib:
+    """Stands in for the CUDA library: records what the binding passes."""
+
+    def __init__(self, n):
+        self.n, self.calls = n, []
+
+    def ppr_graph_n(self, g):
+        return self.n
+
+    def ppr_sssp_query(self, g, src, k, mode, opts, pi, r, counts, stats, stream):
+        self.calls.append(("query", k, pi, r, counts))
+        return binding.PPR_OK
+
+    def ppr_sssp_query_noalloc(self, g, src, k, alpha, lam, pi, sweeps, stream):
+        self.calls.append(("noalloc", k, pi))
+        return binding.PPR_OK
+
+    def ppr_model_train_step(self, m, src, k, labels, lr, loss, stream):
+        self.calls.append(("train_step", k, labels))
+        return binding.PPR_OK
+
+    def ppr_model_estimate(self, m, src, k, out, stream):
+        self.calls.append(("estimate", k, out))
+        return binding.PPR_OK
+
+    def ppr_model_free(self, m):
+        pass
+
+
+def test_query_marshalling_checks_buffers_against_the_graph(monkeypatch):
+    k, n = 4, 9
+    fake = _RecordingLib(n)
+    monkeypatch.setattr(binding, "load_library", lambda build=True: fake)
+    pi, r = np.zeros((k, n)), np.zeros((k, n))
+    counts = np.zeros((k, n), dtype=np.uint32)
+    st = binding.ppr_sssp_query(0x1000, np.arange(k), binding.PPR_APPROX, binding.ppr_query_opts(), pi, r, counts)
+    assert len(st) == k
+    assert fake.calls == [("query", k, pi.ctypes.data, r.ctypes.data, counts.ctypes.data)]
+    binding.ppr_sssp_query_noalloc(0x1000, np.arange(k), pi)
+    assert fake.calls[-1] == ("noalloc", k, pi.ctypes.data)
+    with pytest.raises(ValueError):      # rows sized for another graph: rejected before the call
+        binding.ppr_sssp_query(0x1000, np.arange(k), binding.PPR_HP, binding.ppr_query_opts(), np.zeros((k, n - 1)))
+    with pytest.raises(TypeError):
+        binding.ppr_sssp_query(0x1000, np.arange(k), binding.PPR_APPROX, binding.ppr_query_opts(), pi,
+                               out_walk_counts=np.zeros((k, n)))
+    assert len(fake.calls) == 2
+
+
+def test_model_marshalling_checks_labels_and_outputs(monkeypatch):
+    k, n = 2, 5
+    fake = _RecordingLib(n)
+    monkeypatch.setattr(binding, "load_library", lambda build=True: fake)
+
+    class _G:
+        pass
+    g = _G()
+    g.n = n
+    m = binding.Model(g, handle=0x2000)
+    labels = np.ones((k, n))
+    m.train_step([0, 1], labels, lr=1e-3)
+    assert fake.calls[-1] == ("train_step", k, labels.ctypes.data)
+    x = m.estimate([0, 1])
+    assert x.shape == (k, n) and fake.calls[-1] == ("estimate", k, x.ctypes.data)
+    with pytest.raises(TypeError):
+        m.train_step([0, 1], labels.astype(np.float32))
+    with pytest.raises(ValueError):
+        m.estimate([0, 1, 2], out=np.zeros((2, n)))
+    assert len(fake.calls) == 2
+    m.handle = None
