@@ -214,6 +214,27 @@ def test_residual_identity():
     assert np.abs(O.residual(g, s, exact, ALPHA)).sum() < 1e-12
 
 
+def test_certificate_of_one_exact_pass():
+    """The stopping rule of every high-precision mode: for any estimate x and
+    x' = alpha e_s + (1-alpha) x P (one exact synchronous pass),
+    ||pi - x'||_1 <= (1-alpha) ||x' - x||_1 / alpha, and the pass contracts the
+    error by (1-alpha).  Checked against LAPACK on estimates of every kind the
+    library meets: positive, signed, under or over mass, near the answer."""
+    g = O.Graph(*gen.chung_lu(150, 1500, 2.2, seed=12))
+    P = dense_P(g)
+    s = 9
+    exact = lapack_ppr(g, s)
+    e_s = np.eye(g.n)[s]
+    rng = np.random.default_rng(5)
+    starts = [np.zeros(g.n), rng.random(g.n) / g.n, rng.normal(0, 1e-3, g.n),
+              exact + rng.normal(0, 1e-9, g.n), 2.0 * exact, np.abs(rng.standard_cauchy(g.n))]
+    for x in starts:
+        x1 = ALPHA * e_s + (1 - ALPHA) * x @ P
+        err1 = np.abs(exact - x1).sum()
+        assert err1 <= (1 - ALPHA) * np.abs(x1 - x).sum() / ALPHA * (1 + 1e-12) + 1e-15
+        assert err1 <= (1 - ALPHA) * np.abs(exact - x).sum() * (1 + 1e-12) + 1e-15
+
+
 # ------------------------------------------------------------------ Philox
 def test_philox_known_answers():
     for row in read_golden("philox4x32_10_kat.txt"):
