@@ -48,3 +48,15 @@ def test_sources_and_subgraph():
     srp, sci = gen.bfs_subgraph(rp, ci, 0, 200, seed=1)
     assert len(srp) == 201
     check_clean(srp, sci)
+
+
+def test_benchmark_workload_is_fixed():
+    """The 64-source R-MAT scale-20 workload the benchmark and the parity tests
+    share: its size after cleaning, a checksum of the CSR and of the sources.
+    A change in the generator changes every recorded measurement."""
+    import hashlib
+    rp, ci = gen.rmat(20, 16, seed=1)
+    assert (len(rp) - 1, len(ci)) == (1_048_576, 16_586_703)
+    assert hashlib.sha256(rp.tobytes() + ci.tobytes()).hexdigest()[:16] == "6af68c985594cb03"
+    s = gen.sources(len(rp) - 1, 64, seed=2)
+    assert s[:4].tolist() == [577067, 931816, 260467, 971048] and int(s.sum()) == 36578074
