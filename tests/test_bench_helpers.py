@@ -28,8 +28,14 @@ def test_sweep_bytes():
 
 
 def test_peak_is_the_measured_copy_bandwidth():
+    """The measured copy bandwidth when the machine's peaks file is present,
+    else the stated fallback, labelled as such."""
+    path = bench.os.path.join(bench.ROOT, "MEASURED_PEAKS.json")
     peak, kind = bench.peaks()
-    with open(bench.os.path.join(bench.ROOT, "MEASURED_PEAKS.json")) as f:
+    if not bench.os.path.exists(path):
+        assert (peak, kind) == (6800.0, "fallback")
+        return
+    with open(path) as f:
         assert peak == float(json.load(f)["hbm_gbs"]) and kind == "measured"
 
 
