@@ -284,6 +284,21 @@ np.save(os.environ["PHILOX_OUT"], np.stack([ctr.T.reshape(-1), out.view(torch.in
         assert list(O.philox4x32_10(c, [0x1234567, 0x89ABCDE])) == list(o)
 
 
+def test_philox_words_are_uniform():
+    """Chi-square of Philox-4x32-10 output over consecutive counters, as the
+    walks use it (counter = walk id, step block): the top 4 bits of each of
+    the four words, and the stop test's rate against floor(alpha 2^32)."""
+    from scipy.stats import chi2
+    words = np.array([O.philox4x32_10([w, 0, t, 3], [0x5EED, 0]) for w in range(2500) for t in range(4)],
+                     dtype=np.uint64)
+    for j in range(4):
+        hist = np.bincount((words[:, j] >> 28).astype(np.int64), minlength=16)
+        expect = len(words) / 16
+        assert chi2.sf(((hist - expect) ** 2 / expect).sum(), 15) > 1e-6, j
+    stop = (words[:, [0, 2]] < np.uint64(int(ALPHA * 2**32))).mean()
+    assert abs(stop - ALPHA) < 5 * math.sqrt(ALPHA * (1 - ALPHA) / (2 * len(words)))
+
+
 # --------------------------------------------------------------- SpeedPPR
 def test_walk_endpoints_follow_ppr():
     """An alpha-walk from v stops at u with probability pi(v, u) (Sec. 2).
