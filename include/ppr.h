@@ -80,7 +80,9 @@ typedef struct {
                               scanThreshold"): switch once a frontier level holds more
                               than this many out-edges over the tile; -1 = auto, 0 = no
                               queue phase (sweeps from the start) */
-  int32_t max_sweeps;      /* bound on dense sweeps; 0 = 4*ceil(ln lambda/ln(1-alpha))+64 */
+  int32_t max_sweeps;      /* bound on dense sweeps; 0 = 4*ceil(ln lambda/ln(1-alpha))+64;
+                              at most 131072 (a larger bound, or an alpha so small that
+                              the default exceeds it, is PPR_ERR_ARG) */
   int32_t flags;           /* OR of the PPR_FLAG_* bits above.  PPR_FLAG_PARTIAL (HP)
                               returns the estimate after exactly max_sweeps passes
                               without certifying lambda (the stats' final_l1_residual
@@ -172,22 +174,30 @@ ppr_status ppr_sssp_query(ppr_graph* g, const int32_t* src, int32_t k, ppr_mode 
  * own allocator, or a process that has already reserved all free memory in a
  * caching pool.  ppr_sssp_query grows a per-graph workspace with cudaMalloc;
  * this call instead runs a simpler variant of the pull sweep (zero start,
- * every node pushed each pass, Sec. 4.1 / Lemma 1) whose scratch is one
- * 16 MiB array compiled into the library, and it calls no allocation routine.
+ * every node pushed each pass) whose scratch is one 16 MiB array compiled into
+ * the library, and it calls no allocation routine.
  *   src: host int32[k]; out_pi: DEVICE k x n float64 (caller-owned);
  *   out_sweeps: optional host int32[k] (passes run for each source).
  *   Result: ||pi_hat - pi||_1 <= lambda for every source, as ppr_sssp_query.
- * Limit: n * min(k, 8) rounded to a power of two, times 24 bytes, plus a few
- * kilobytes, must fit in the 16 MiB (about 87,000 nodes for 8 sources at a
- * time, 690,000 for one); larger graphs return PPR_ERR_ARG with a message.
+ * Limit: sources are solved k_tile at a time, k_tile = min(k, 8) rounded down
+ * to 1, 2, 4 or 8.  n * k_tile * 24 bytes plus the residual sums,
+ * (max_sweeps + 1) * k_tile * 8 bytes with max_sweeps =
+ * 4 ceil(ln lambda / ln(1 - alpha)) + 64, must fit in the 16 MiB (about
+ * 87,000 nodes at k_tile = 8, 690,000 at k_tile = 1 for alpha = 0.2); larger
+ * graphs return PPR_ERR_ARG with a message, and so does an alpha so small that
+ * max_sweeps would exceed 131072.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before capturing any stream on the device.  All calls share the one array
  * (it keeps the last call's contents; the call clears what must start at
  * zero), so calls that overlap on the GPU -- other threads, other streams --
- * race and must be serialised by the caller.  The graph itself is allocated
- * by ppr_graph_load as usual.  Errors: PPR_ERR_ARG, PPR_ERR_NOT_CONVERGED,
- * PPR_ERR_CUDA.
+ * race and must be serialised by the caller.  The graph's per-node scale
+ * factors depend on alpha and are rewritten (on the call's stream) when a
+ * call brings an alpha other than the last one used on that graph: calls with
+ * different alphas on one graph must therefore be serialised against every
+ * query entry point (ppr_sssp_query included), not only against each other.
+ * The graph itself is allocated by ppr_graph_load as usual.  Errors:
+ * PPR_ERR_ARG, PPR_ERR_NOT_CONVERGED, PPR_ERR_CUDA.
  */
 ppr_status ppr_sssp_query_noalloc(ppr_graph* g, const int32_t* src, int32_t k, double alpha, double lambda,
                                   double* out_pi, int32_t* out_sweeps, void* cuda_stream);

@@ -331,7 +331,8 @@ static ppr_status build_plan(ppr_graph* g, int kt, Plan& p, cudaStream_t st) {
 
 template <int KT>
 static void launch_sweep(const SweepArgs& a, int grid, cudaStream_t st) {
-  sweep_kernel<KT><<<grid, 256, 0, st>>>(a);
+  if (a.z_out == a.z_in) sweep_kernel<KT, true><<<grid, 256, 0, st>>>(a);
+  else sweep_kernel<KT, false><<<grid, 256, 0, st>>>(a);
 }
 
 // Algorithm 3's epochs from the push state (r, pi): epoch i pushes, in full
@@ -557,7 +558,7 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
       double& rate = rates[prec];
       const double known = rate > 0.0 ? rate : rates[1 - prec];
       const double cr = known > 0.0 ? known : (1.0 - alpha);
-      int S = std::max((int)std::ceil(std::log(phase_goal / F) / std::log(cr) - 1e-12), 1);
+      int S = batch_passes(phase_goal, F, cr, t.max_sweeps);
       if (known <= 0.0) S = std::min(S, 16);  // learn the rate first
       if (corr_pending) S = t.corr;          // the passes the correction model was trained after
       if (sweeps + S + 1 > t.max_sweeps) {
@@ -674,7 +675,7 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
       sa.n_items = plan.n_items_all;
       sa.resid = resid;
       PPR_CUDA_TRY(cudaEventRecord(es0, st));
-      sweep_kernel<KT><<<sweep_grid, 256, 0, st>>>(sa);
+      sweep_kernel<KT, false><<<sweep_grid, 256, 0, st>>>(sa);
       PPR_CUDA_TRY(cudaEventRecord(es1, st));
       PPR_CUDA_TRY(cudaGetLastError());
       ++sweeps;
@@ -737,8 +738,15 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
   double* r_view = out_r ? static_cast<double*>(device_view(out_r)) : nullptr;
   const bool pi_on_host = pi_view == nullptr;
   const bool r_on_host = out_r && r_view == nullptr;
-  const int max_sweeps = o.max_sweeps > 0 ? o.max_sweeps
-                                          : 4 * (int)std::ceil(std::log(lambda) / std::log(1.0 - alpha)) + 64;
+  if (o.max_sweeps > kMaxSweepsCap) {
+    set_error("max_sweeps %d above the limit of %d passes", o.max_sweeps, kMaxSweepsCap);
+    return PPR_ERR_ARG;
+  }
+  const int max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : sweep_limit(alpha, lambda);
+  if (max_sweeps < 1) {
+    set_error("alpha %g is too small for lambda %g: more than %d passes", alpha, lambda, kMaxSweepsCap);
+    return PPR_ERR_ARG;
+  }
 
   // admission: state for one tile plus staging of host outputs
   size_t need = 4 * cells * 8 + cells * 4 * 4 + cells * 16 + (size_t)m * KT / kPushChunk * 8 + (size_t)max_sweeps * KT * 8;
@@ -814,7 +822,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
   const int64_t switch_edges = o.switch_edges >= 0 ? o.switch_edges
                                                    : (int64_t)((tuned_frac >= 0 ? tuned_frac : 0.02) * (double)m * KT);
   int bps = 0;
-  PPR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, sweep_kernel<KT>, 256, 0));
+  PPR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, sweep_kernel<KT, false>, 256, 0));
   const int sweep_grid = sm_count() * std::max(bps, 1);
 
 
@@ -1043,9 +1051,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
         // the observed rate (faster after a learned correction) predicts the
         // passes, and every stop is still certified by a measurement.
         const double cr = rate > 0.0 ? rate : (1.0 - alpha);
-        int S = (!std::isfinite(R) || R <= lambda) ? 1
-                                                    : (int)std::ceil(std::log(lambda / R) / std::log(cr) - 1e-12);
-        S = std::max(S, 1);
+        int S = (!std::isfinite(R) || R <= lambda) ? 1 : batch_passes(lambda, R, cr, max_sweeps);
         if (rate <= 0.0 && probe_next) S = std::min(S, probe_len);
         if (corr > 0 && !corrected) S = std::max(corr - sweeps, 1);  // passes before the correction
         if (partial) S = std::max(max_sweeps - sweeps, 0);

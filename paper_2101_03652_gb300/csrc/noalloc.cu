@@ -143,7 +143,11 @@ static ppr_status run_noalloc(ppr_graph* g, const int32_t* src, int32_t k, doubl
                               double* out_pi, int32_t* out_sweeps, cudaStream_t st) {
   const int64_t n = g->n, m = g->m;
   const size_t cells = (size_t)n * KT;
-  const int max_sweeps = 4 * (int)std::ceil(std::log(lambda) / std::log(1.0 - alpha)) + 64;
+  const int max_sweeps = sweep_limit(alpha, lambda);
+  if (max_sweeps < 1) {
+    set_error("alpha %g is too small for lambda %g: more than %d passes", alpha, lambda, kMaxSweepsCap);
+    return PPR_ERR_ARG;
+  }
   const size_t need = 3 * cells * 8 + (size_t)(max_sweeps + 1) * KT * 8;
   if (need > kNoAllocScratchBytes) {
     set_error("graph too large for the no-allocation entry point: %zu bytes of scratch needed "
@@ -184,8 +188,7 @@ static ppr_status run_noalloc(ppr_graph* g, const int32_t* src, int32_t k, doubl
     int sweeps = 0;
     double R = 1.0;  // ||r(x0)||_1 of the zero start
     while (true) {
-      int S = R <= lambda ? 1 : (int)std::ceil(std::log(lambda / R) / std::log(1.0 - alpha) - 1e-12);
-      S = std::max(S, 1);
+      const int S = R <= lambda ? 1 : batch_passes(lambda, R, 1.0 - alpha, max_sweeps);
       if (sweeps + S > max_sweeps) {
         set_error("sweep limit %d reached", max_sweeps);
         return PPR_ERR_NOT_CONVERGED;

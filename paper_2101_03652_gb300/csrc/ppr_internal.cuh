@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include <string>
 #include <vector>
 
@@ -29,6 +31,25 @@ void clear_error();
     ppr_status s_ = (expr);           \
     if (s_ != PPR_OK) return s_;      \
   } while (0)
+
+// Passes a high-precision query may run: 4 ceil(ln lambda / ln(1 - alpha)) + 64
+// (four times the zero-start PowItr count of Eq. 6, plus slack), computed in
+// double.  Returns -1 when that exceeds kMaxSweepsCap, i.e. when alpha is so
+// small for lambda that the count would not fit the per-pass buffers.
+constexpr int kMaxSweepsCap = 1 << 17;
+inline int sweep_limit(double alpha, double lambda) {
+  const double s = 4.0 * std::ceil(std::log(lambda) / std::log(1.0 - alpha)) + 64.0;
+  return (s >= 1.0 && s <= (double)kMaxSweepsCap) ? (int)s : -1;
+}
+
+// Passes of a batch: ceil(ln(goal / F) / ln(rate)), at least 1, computed in
+// double and clamped to cap + 1 so that the cast cannot overflow (a caller that
+// finds more than cap passes reports the sweep limit).
+inline int batch_passes(double goal, double F, double rate, int cap) {
+  const double s = std::ceil(std::log(goal / F) / std::log(rate) - 1e-12);
+  if (!(s >= 1.0)) return 1;
+  return s > (double)cap ? cap + 1 : (int)s;
+}
 
 // Fixed-point format of the high-precision path: unsigned Q1.63, value = raw * 2^-63.
 constexpr double kFixOne = 9223372036854775808.0;  // 2^63

@@ -83,9 +83,16 @@ struct Raw<bf16, 2> { typedef unsigned int type; };
 template <>
 struct Raw<bf16, 1> { typedef unsigned short type; };
 
-template <typename T, int V>
+// Loads of z_e.  An in-place pass (every unmeasured pass) writes the buffer
+// it gathers from, so its loads go through L2 (ld.global.cg, coherent across
+// SMs); the read-only path (ld.global.nc) serves only buffers that no thread
+// writes during the kernel (the measured pass reads one buffer and writes the
+// other).
+template <typename T, int V, bool COH = false>
 __device__ __forceinline__ typename Raw<T, V>::type ld_raw(const T* p) {
-  return __ldg(reinterpret_cast<const typename Raw<T, V>::type*>(p));
+  const auto* q = reinterpret_cast<const typename Raw<T, V>::type*>(p);
+  if constexpr (COH) return __ldcg(q);
+  else return __ldg(q);
 }
 template <typename T, int V>
 __device__ __forceinline__ typename Raw<T, V>::type zero_raw() {
@@ -117,11 +124,11 @@ __device__ __forceinline__ void add_raw(float (&acc)[V], const typename Raw<T, V
   }
 }
 
-template <typename T, int V>
+template <typename T, int V, bool COH>
 __device__ __forceinline__ void ld_row(const T* p, float (&v)[V]) {
 #pragma unroll
   for (int q = 0; q < V; ++q) v[q] = 0.f;
-  add_raw<T, V>(v, ld_raw<T, V>(p));
+  add_raw<T, V>(v, ld_raw<T, V, COH>(p));
 }
 
 // FP32 row piece of V values (V up to 8)
@@ -223,13 +230,13 @@ __device__ __forceinline__ void refine_epilogue(const RefArgs& a, int u, int slo
   if (a.relax != 1.f) {
     // over-relaxed in-place pass (ze_in == ze_out): this row's own old value
     float zo[V];
-    ld_row<T, V>(static_cast<const T*>(a.ze_in) + base, zo);
+    ld_row<T, V, !MEAS>(static_cast<const T*>(a.ze_in) + base, zo);
 #pragma unroll
     for (int q = 0; q < V; ++q) zn[q] = zo[q] + a.relax * (zn[q] - zo[q]);
   }
   if (MEAS) {
     float zo[V];
-    ld_row<T, V>(static_cast<const T*>(a.ze_in) + base, zo);
+    ld_row<T, V, false>(static_cast<const T*>(a.ze_in) + base, zo);
     const float inv = d / a.one_minus_alpha;
 #pragma unroll
     for (int q = 0; q < V; ++q) res[q] += fabsf(zn[q] - zo[q]) * inv;
@@ -238,7 +245,7 @@ __device__ __forceinline__ void refine_epilogue(const RefArgs& a, int u, int slo
   if (a.e_out) st_f32<V>(a.e_out + base, e);
 }
 
-template <int KT, typename T>
+template <int KT, typename T, bool COH>
 __device__ __forceinline__ void refine_gather_warp(const RefArgs& a, int e_begin, int e_end, int lane, int slot,
                                                    float (&acc)[RLay<KT, T>::V]) {
   constexpr int V = RLay<KT, T>::V, L = RLay<KT, T>::L, EPW = RLay<KT, T>::EPW, UNR = RefTune<KT, T, false>::UNR;
@@ -253,7 +260,7 @@ __device__ __forceinline__ void refine_gather_warp(const RefArgs& a, int e_begin
     typename Raw<T, V>::type t[UNR];
 #pragma unroll
     for (int q = 0; q < UNR; ++q)
-      t[q] = v[q] >= 0 ? ld_raw<T, V>(z + (size_t)v[q] * KT + slot * V) : zero_raw<T, V>();
+      t[q] = v[q] >= 0 ? ld_raw<T, V, COH>(z + (size_t)v[q] * KT + slot * V) : zero_raw<T, V>();
 #pragma unroll
     for (int q = 0; q < UNR; ++q) add_raw<T, V>(acc, t[q]);
   }
@@ -276,7 +283,7 @@ __global__ void __launch_bounds__(256, (RefTune<KT, T, MEAS>::MIN_BLOCKS)) refin
       // piece of a split row; the last piece to arrive finishes the row
       const int u = w.y;
       float acc[V] = {};
-      refine_gather_warp<KT, T>(a, w.z, w.w, lane, slot, acc);
+      refine_gather_warp<KT, T, !MEAS>(a, w.z, w.w, lane, slot, acc);
 #pragma unroll
       for (int off = L; off < 32; off <<= 1)
 #pragma unroll
@@ -302,7 +309,7 @@ __global__ void __launch_bounds__(256, (RefTune<KT, T, MEAS>::MIN_BLOCKS)) refin
       for (int u = w.y; u < w.z; ++u) {
         const auto pre = refine_prefetch<KT, T>(a, u, slot);
         float acc[V] = {};
-        refine_gather_warp<KT, T>(a, __ldg(&a.in_rp[u]), __ldg(&a.in_rp[u + 1]), lane, slot, acc);
+        refine_gather_warp<KT, T, !MEAS>(a, __ldg(&a.in_rp[u]), __ldg(&a.in_rp[u + 1]), lane, slot, acc);
 #pragma unroll
         for (int off = L; off < 32; off <<= 1)
 #pragma unroll
@@ -316,7 +323,7 @@ __global__ void __launch_bounds__(256, (RefTune<KT, T, MEAS>::MIN_BLOCKS)) refin
         float acc[V] = {};
 #pragma unroll RefTune<KT, T, MEAS>::UNR
         for (int e = __ldg(&a.in_rp[u]); e < e1; ++e)
-          add_raw<T, V>(acc, ld_raw<T, V>(z + (size_t)__ldg(&a.in_ci[e]) * KT + slot * V));
+          add_raw<T, V>(acc, ld_raw<T, V, !MEAS>(z + (size_t)__ldg(&a.in_ci[e]) * KT + slot * V));
         refine_epilogue<KT, T, MEAS>(a, u, slot, pre, acc, res);
       }
     }

@@ -59,14 +59,17 @@ struct Lay {
   static constexpr int EPW = 32 / L;         // edges a warp gathers per step
 };
 
-template <int V>
+// COH: the buffer is written during the kernel (an in-place pass), so the
+// load goes through L2 (ld.global.cg) instead of the read-only path
+template <int V, bool COH = false>
 __device__ __forceinline__ void ld_vec(const u64* p, u64 (&v)[V]) {
   if constexpr (V == 2) {
-    ulonglong2 t = __ldg(reinterpret_cast<const ulonglong2*>(p));
+    const ulonglong2* q = reinterpret_cast<const ulonglong2*>(p);
+    ulonglong2 t = COH ? __ldcg(q) : __ldg(q);
     v[0] = t.x;
     v[1] = t.y;
   } else {
-    v[0] = __ldg(p);
+    v[0] = COH ? __ldcg(p) : __ldg(p);
   }
 }
 template <int V>
@@ -79,7 +82,7 @@ __device__ __forceinline__ void st_vec(u64* p, const u64 (&v)[V]) {
 }
 
 // finish row u for the V columns of `slot`: x = sum + alpha [u == s], z = x w
-template <int KT>
+template <int KT, bool COH>
 __device__ __forceinline__ void row_epilogue(const SweepArgs& a, int u, int slot, const u64 (&acc)[Lay<KT>::V],
                                              float (&res)[Lay<KT>::V]) {
   constexpr int V = Lay<KT>::V;
@@ -113,7 +116,7 @@ __device__ __forceinline__ void row_epilogue(const SweepArgs& a, int u, int slot
   }
   if (a.resid) {
     u64 zo[V];
-    ld_vec<V>(a.z_in + (size_t)u * KT + slot * V, zo);
+    ld_vec<V, COH>(a.z_in + (size_t)u * KT + slot * V, zo);
 #pragma unroll
     for (int q = 0; q < V; ++q) res[q] += (float)(zn[q] > zo[q] ? zn[q] - zo[q] : zo[q] - zn[q]) * iw;
   }
@@ -125,7 +128,7 @@ __device__ __forceinline__ void row_epilogue(const SweepArgs& a, int u, int slot
 // EPW edges per step (L lanes per edge) and UNR steps are issued before any
 // is consumed, so each lane keeps UNR independent gathers in flight.  The
 // loop bound is warp-uniform; lanes past the end are predicated off.
-template <int KT, int UNR>
+template <int KT, int UNR, bool COH>
 __device__ __forceinline__ void gather_warp(const SweepArgs& a, int e_begin, int e_end, int lane, int slot,
                                             u64 (&acc)[Lay<KT>::V]) {
   constexpr int V = Lay<KT>::V, L = Lay<KT>::L, EPW = Lay<KT>::EPW;
@@ -140,7 +143,7 @@ __device__ __forceinline__ void gather_warp(const SweepArgs& a, int e_begin, int
 #pragma unroll
     for (int q = 0; q < UNR; ++q) {
       if (v[q] >= 0) {
-        ld_vec<V>(a.z_in + (size_t)v[q] * KT + slot * V, t[q]);
+        ld_vec<V, COH>(a.z_in + (size_t)v[q] * KT + slot * V, t[q]);
       } else {
 #pragma unroll
         for (int w = 0; w < V; ++w) t[q][w] = 0;
@@ -153,7 +156,8 @@ __device__ __forceinline__ void gather_warp(const SweepArgs& a, int e_begin, int
   }
 }
 
-template <int KT>
+// INPLACE: z_out == z_in (asynchronous pass), loads of z through L2
+template <int KT, bool INPLACE>
 __global__ void __launch_bounds__(256, 6) sweep_kernel(SweepArgs a) {
   constexpr int V = Lay<KT>::V, L = Lay<KT>::L;
   constexpr int UNR = kUnr;
@@ -174,7 +178,7 @@ __global__ void __launch_bounds__(256, 6) sweep_kernel(SweepArgs a) {
       // last piece of the row to arrive finishes it
       const int u = w.y;
       u64 acc[V] = {};
-      gather_warp<KT, UNR>(a, w.z, w.w, lane, slot, acc);
+      gather_warp<KT, UNR, INPLACE>(a, w.z, w.w, lane, slot, acc);
 #pragma unroll
       for (int off = L; off < 32; off <<= 1)
 #pragma unroll
@@ -192,7 +196,7 @@ __global__ void __launch_bounds__(256, 6) sweep_kernel(SweepArgs a) {
           u64 tot[V];
 #pragma unroll
           for (int q = 0; q < V; ++q) tot[q] = atomicExch(&a.heavy_acc[(size_t)u * KT + slot * V + q], 0ull);
-          row_epilogue<KT>(a, u, slot, tot, res);
+          row_epilogue<KT, INPLACE>(a, u, slot, tot, res);
         }
         if (lane == 0) atomicExch(&a.heavy_cnt[u], 0u);
       }
@@ -200,12 +204,12 @@ __global__ void __launch_bounds__(256, 6) sweep_kernel(SweepArgs a) {
       // medium rows: one warp per row
       for (int u = w.y; u < w.z; ++u) {
         u64 acc[V] = {};
-        gather_warp<KT, UNR>(a, __ldg(&a.in_rp[u]), __ldg(&a.in_rp[u + 1]), lane, slot, acc);
+        gather_warp<KT, UNR, INPLACE>(a, __ldg(&a.in_rp[u]), __ldg(&a.in_rp[u + 1]), lane, slot, acc);
 #pragma unroll
         for (int off = L; off < 32; off <<= 1)
 #pragma unroll
           for (int q = 0; q < V; ++q) acc[q] += __shfl_xor_sync(kFull, acc[q], off);
-        if (lane < L) row_epilogue<KT>(a, u, slot, acc, res);
+        if (lane < L) row_epilogue<KT, INPLACE>(a, u, slot, acc, res);
       }
     } else {
       // light rows: L lanes per row, 32/L consecutive rows at a time (rows are
@@ -216,11 +220,11 @@ __global__ void __launch_bounds__(256, 6) sweep_kernel(SweepArgs a) {
 #pragma unroll 4
         for (int e = __ldg(&a.in_rp[u]); e < e1; ++e) {
           u64 t[V];
-          ld_vec<V>(a.z_in + (size_t)__ldg(&a.in_ci[e]) * KT + slot * V, t);
+          ld_vec<V, INPLACE>(a.z_in + (size_t)__ldg(&a.in_ci[e]) * KT + slot * V, t);
 #pragma unroll
           for (int q = 0; q < V; ++q) acc[q] += t[q];
         }
-        row_epilogue<KT>(a, u, slot, acc, res);
+        row_epilogue<KT, INPLACE>(a, u, slot, acc, res);
       }
     }
   }
