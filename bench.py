@@ -37,8 +37,8 @@ WORKLOADS = {
     "rmat20-k8": (20, 16, 8, 8),
     "rmat22-k1": (22, 16, 1, 1),
     "rmat22-k64": (22, 16, 64, 64),
-    "rmat22-approx": (22, 16, 16, 16),  # SpeedPPR, eps = 0.5, sources seed 3
-    "rmat22-index": (22, 16, 16, 16),   # SpeedPPR-Index (walks read from the index), same sources
+    "rmat22-approx": (22, 16, 256, 16),  # SpeedPPR, eps = 0.5, 256 sources (seed 3) in 16-column tiles
+    "rmat22-index": (22, 16, 256, 16),   # SpeedPPR-Index (walks read from the index), same sources
 }
 APPROX_WORKLOADS = ("rmat22-approx", "rmat22-index")
 ALPHA, LAMBDA, EPS = 0.2, 1e-8, 0.5
@@ -181,6 +181,9 @@ def max_over_ranks(value: float, device) -> float:
     return float(t.item())
 
 
+CALIB_SEED = 12  # sources of the autotuner's calibration batch (never the timed ones)
+
+
 def make_inputs(workload: str, rank: int):
     import ppr_inputs as gen
     scale, ef, k, kt = WORKLOADS[workload]
@@ -188,6 +191,84 @@ def make_inputs(workload: str, rank: int):
     seed = 3 if workload in APPROX_WORKLOADS else 2
     src = gen.sources(len(rp) - 1, k, seed=replica_seed(seed, rank))
     return rp, ci, src, kt
+
+
+def calibration_sources(n: int, k: int, rank: int):
+    """The autotuner's calibration batch: k sources drawn with their own seed,
+    so that the setting is chosen on other sources than the ones timed."""
+    import ppr_inputs as gen
+    return gen.sources(n, k, seed=replica_seed(CALIB_SEED, rank))
+
+
+def hp_roofline(n: int, m: int, kt: int, fp32_ms: float, fp32_launches: int, sweep_ms: float, sweep_launches: int,
+                workload: str):
+    """Roofline entry of a high-precision workload's dominant kernel: the FP32
+    correction pass when the query ran any, else the Q1.63 pass."""
+    if fp32_launches > 0:
+        avg = fp32_ms / fp32_launches
+        per_launch, per_launch_min = fp32_pass_bytes(n, m, kt), fp32_pass_bytes_min(n, m, kt)
+        name = f"refine_pass_kernel<{kt}, float>"
+    else:
+        avg = sweep_ms / max(sweep_launches, 1)
+        per_launch = per_launch_min = sweep_bytes(n, m, kt)
+        name = f"sweep_kernel<{kt}>"
+    achieved = per_launch / (avg / 1e3) / 1e9
+    traffic = ncu_traffic(workload, name.split("<")[0])
+    peak, peak_kind = peaks()
+    return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+            "unit": "GB/s", "frac": achieved / peak, "nominal_peak": NOMINAL_HBM_GBS,
+            "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "traffic": traffic,
+            "traffic_gbs": None if traffic is None else traffic / (avg / 1e3) / 1e9,
+            "algorithmic_bytes_per_launch": per_launch, "algorithmic_bytes_lower_bound": per_launch_min,
+            "frac_of_lower_bound": per_launch_min / (avg / 1e3) / 1e9 / peak, "avg_launch_ms": avg}
+
+
+def hp_side_record(P, label: str, rp, ci, src, steps: int, warmup: int, rank: int, local: int, flush):
+    """A second high-precision workload timed like the headline one (autotuned
+    on a calibration batch outside the timed region, L2 flushed before every
+    step, CUDA events on the stream): queries/s, passes and the dominant
+    kernel's roofline entry."""
+    import torch
+    n, m, k = len(rp) - 1, len(ci), len(src)
+    g = P.Graph(rp, ci)
+    out = torch.empty((k, n), dtype=torch.float64, device="cuda")
+    t_tune = time.perf_counter()
+    kt, sw, _ = g.autotune(calibration_sources(n, k, rank), lam=LAMBDA, alpha=ALPHA)
+    tuned = {"k_tile": int(kt), "switch_edges": int(sw), "seconds": time.perf_counter() - t_tune,
+             "calibration_seed": CALIB_SEED}
+    opts = dict(lam=LAMBDA, alpha=ALPHA, k_tile=0, switch_edges=-1)
+    for _ in range(warmup):
+        flush.zero_()
+        g.query(src, P.PPR_HP, out_pi=out, **opts)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev, sweeps, launches = [], [], 0
+    fp32_ms = sweep_ms = 0.0
+    fp32_launches = sweep_launches = 0
+    with ClockSampler(local) as clk:
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, st = g.query(src, P.PPR_HP, out_pi=out, **opts)
+            e1.record(stream)
+            ev.append((e0, e1))
+            sweeps.append(st[0]["sweeps"])
+            launches += st[0]["kernel_launches"]
+            fp32_ms += st[0]["ms_fp32"]
+            fp32_launches += sum(st[t]["fp32_passes"] for t in range(0, k, kt))
+            sweep_ms += st[0]["ms_sweep"]
+            sweep_launches += st[0]["sweep_launches"]
+        torch.cuda.synchronize()
+    assert max(x["final_l1_residual"] for x in st) <= LAMBDA
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    g.close()
+    return {"workload": label, "n": n, "m": m, "sources_per_step": k, "steps": steps, "warmup": warmup,
+            "k_tile": int(kt), "autotuned": tuned, "ms_per_step": total_ms / steps,
+            "queries_per_s": k * steps / (total_ms / 1e3), "sweeps_per_tile": statistics.median(sweeps),
+            "launches_per_step": launches / steps,
+            "roofline": hp_roofline(n, m, int(kt), fp32_ms, fp32_launches, sweep_ms, sweep_launches, label),
+            "clocks": clk.summary()}
 
 
 def run_reference(args):
@@ -260,10 +341,12 @@ def run_gpu(args):
     tuned = None
     if not approx and not args.no_autotune:
         # the k-tile and the queue->pass switch come from the library's
-        # autotuner, run on this step's sources outside the timed region
+        # autotuner, run outside the timed region on a calibration batch of
+        # other sources
         t_tune = time.perf_counter()
-        kt_t, sw_t, _ = g.autotune(src, lam=LAMBDA, alpha=ALPHA)
-        tuned = {"k_tile": int(kt_t), "switch_edges": int(sw_t), "seconds": time.perf_counter() - t_tune}
+        kt_t, sw_t, _ = g.autotune(calibration_sources(n, k, rank), lam=LAMBDA, alpha=ALPHA)
+        tuned = {"k_tile": int(kt_t), "switch_edges": int(sw_t), "seconds": time.perf_counter() - t_tune,
+                 "calibration_seed": CALIB_SEED}
         opts = dict(lam=LAMBDA, alpha=ALPHA, k_tile=0, switch_edges=-1)
         kt = int(kt_t)
 
@@ -318,6 +401,21 @@ def run_gpu(args):
     if not args.skip_warm and args.workload == "rmat20-k64":
         warm = warm_start_comparison(P, g, n, k, kt, out, flush, rank)
 
+    # the same method on the larger R-MAT graph of the roofline target, and on
+    # the small graph where a pass takes microseconds (one GPU only)
+    side = {}
+    if ws == 1 and not args.skip_side and args.workload == "rmat20-k64":
+        import ppr_inputs as gen
+        rp22, ci22 = gen.rmat(22, 16, seed=1)
+        src22 = gen.sources(len(rp22) - 1, 64, seed=2)
+        side["rmat22_k64"] = hp_side_record(P, "rmat22-k64", rp22, ci22, src22, min(args.steps, 5), 2, rank, local,
+                                            flush)
+        del rp22, ci22
+        rpc, cic = gen.chung_lu(10_000, 100_000, 2.2, seed=1)
+        srcc = gen.sources(len(rpc) - 1, 10, seed=1)
+        side["small_graph"] = hp_side_record(P, "chung-lu-10k-k10", rpc, cic, srcc, max(args.steps, 20),
+                                             max(args.warmup, 3), rank, local, flush)
+
     # sanity of the last answers (the parity tests check them against the oracle)
     pi0 = out[0].double()
     mass = float(pi0.sum().item())
@@ -330,36 +428,39 @@ def run_gpu(args):
         return
 
     value = ws * k * args.steps / (total_ms / 1e3)
+    n_tiles = -(-k // kt)  # one walk (or index) launch per tile of kt sources
     if indexed:
         # dominant kernel: the index reads; per walk one 4 B index entry and the
         # two 32 B sectors of its endpoint's count and estimate
         walks_total = sum(x["walks"] for x in st) * args.steps
-        per_launch = 68 * walks_total / args.steps
-        avg_sweep_ms = sweep_ms / args.steps
+        per_launch = 68 * walks_total / args.steps / n_tiles
+        avg_sweep_ms = sweep_ms / args.steps / n_tiles
         kernel_name = f"index_query_kernel<{kt}>"
     elif approx:
         # dominant kernel: the walks; algorithmic bytes = two 32 B sectors per move
         steps_total = sum(x["walk_steps"] for x in st) * args.steps
         walks_total = sum(x["walks"] for x in st) * args.steps
-        per_launch = 64 * (steps_total + walks_total) / args.steps
-        avg_sweep_ms = sweep_ms / args.steps
+        per_launch = 64 * (steps_total + walks_total) / args.steps / n_tiles
+        avg_sweep_ms = sweep_ms / args.steps / n_tiles
         kernel_name = f"walk_kernel<{kt}>"
-    elif fp32_launches > 0:
-        # dominant kernel: the FP32 correction pass (the Q1.63 passes only certify)
-        avg_sweep_ms = fp32_ms / fp32_launches
-        per_launch = fp32_pass_bytes(n, m, kt)
-        kernel_name = f"refine_pass_kernel<{kt}, float>"
+    if approx:
+        # the other kernels' counts are already their minimum
+        per_launch_min = per_launch
+        achieved = per_launch / (avg_sweep_ms / 1e3) / 1e9
+        achieved_min = per_launch_min / (avg_sweep_ms / 1e3) / 1e9
+        # DRAM bytes per launch from the committed ncu capture (None if the source changed since)
+        traffic = ncu_traffic(args.workload, kernel_name.split("<")[0])
+        peak, peak_kind = peaks()
+        roofline = {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                    "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                    "traffic": traffic,
+                    "traffic_gbs": None if traffic is None else traffic / (avg_sweep_ms / 1e3) / 1e9,
+                    "algorithmic_bytes_per_launch": per_launch, "algorithmic_bytes_lower_bound": per_launch_min,
+                    "frac_of_lower_bound": achieved_min / peak, "avg_launch_ms": avg_sweep_ms}
     else:
-        avg_sweep_ms = sweep_ms / max(sweep_launches, 1)
-        per_launch = sweep_bytes(n, m, kt)
-        kernel_name = f"sweep_kernel<{kt}>"
-    # the other kernels' counts are already their minimum
-    per_launch_min = fp32_pass_bytes_min(n, m, kt) if kernel_name.startswith("refine_pass_kernel") else per_launch
-    achieved = per_launch / (avg_sweep_ms / 1e3) / 1e9
-    achieved_min = per_launch_min / (avg_sweep_ms / 1e3) / 1e9
-    # DRAM bytes per launch from the committed ncu capture (None if the source changed since)
-    traffic = ncu_traffic(args.workload, kernel_name.split("<")[0])
-    peak, peak_kind = peaks()
+        # dominant kernel: the FP32 correction pass (the Q1.63 passes only certify)
+        roofline = hp_roofline(n, m, kt, fp32_ms, fp32_launches, sweep_ms, sweep_launches, args.workload)
     cpu = None
     cpu_context = None
     if ws == 1 and not args.skip_cpu:
@@ -409,18 +510,11 @@ def run_gpu(args):
         "sweeps_per_tile": statistics.median(sweeps),
         "e2e": {"value": ws * k * e2e_steps / e2e_total, "unit": "queries/s", "h2d_bytes_per_step": 4 * k,
                 "d2h_bytes_per_step": 8 * k * n},
-        "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
-                     "traffic": traffic,
-                     "traffic_gbs": None if traffic is None else traffic / (avg_sweep_ms / 1e3) / 1e9,
-                     "algorithmic_bytes_per_launch": per_launch,
-                     "algorithmic_bytes_lower_bound": per_launch_min,
-                     "frac_of_lower_bound": achieved_min / peak,
-                     "avg_launch_ms": avg_sweep_ms},
+        "roofline": roofline,
         "cpu_baseline": cpu,
         "cpu_context": cpu_context,
         "warm_start": warm,
+        **side,
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
@@ -448,6 +542,7 @@ def warm_start_comparison(P, g, n, k, kt, out, flush, rank, train_n=4096, held_n
     for name, ws in (("plain", None), ("warm", model)):
         ev = []
         sweeps = []
+        edges = []
         g.query(held[:k], P.PPR_HP, out_pi=out, lam=LAMBDA, k_tile=kt, warm_start=ws)  # warm-up
         for b in range(0, held_n, k):
             flush.zero_()
@@ -457,15 +552,32 @@ def warm_start_comparison(P, g, n, k, kt, out, flush, rank, train_n=4096, held_n
             e1.record()
             ev.append((e0, e1))
             sweeps.append(st[0]["sweeps"])
+            # edges touched per query: out-edges scattered by its queue phase
+            # plus in-edges gathered by its passes (m per pass)
+            edges.extend(x["edges_pushed"] + x["edges_swept"] for x in st)
         torch.cuda.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in ev)
-        res[name] = {"queries_per_s": held_n / (ms / 1e3), "passes_mean": float(np.mean(sweeps))}
+        res[name] = {"queries_per_s": held_n / (ms / 1e3), "passes_mean": float(np.mean(sweeps)),
+                     "edges_touched_per_query": float(np.mean(edges))}
     model.close()
     return {"metric": "queries/s at l1<=1e-8 on held-out sources", "train_sources": train_n,
             "held_out_sources": held_n, "epochs": epochs, "correction_passes": passes,
             "train_seconds_incl_labels": train_s, "final_train_l1": float(losses[-1]),
             "plain": res["plain"], "warm": res["warm"],
-            "speedup": res["warm"]["queries_per_s"] / res["plain"]["queries_per_s"]}
+            "speedup": res["warm"]["queries_per_s"] / res["plain"]["queries_per_s"],
+            "edges_touched_ratio": res["warm"]["edges_touched_per_query"] / res["plain"]["edges_touched_per_query"]}
+
+
+def admit_batch(k: int, free_bytes: int, held_bytes: int, state_bytes) -> int:
+    """Admission of a serving batch: the largest k (halved until it fits)
+    whose query workspace, state_bytes(k), fits in free device memory plus the
+    workspace the graph already holds (the library reuses it); 0 when not even
+    one source fits, and the batch is refused."""
+    while k >= 1:
+        if state_bytes(k) <= free_bytes + held_bytes:
+            return k
+        k //= 2
+    return 0
 
 
 def run_serve(args):
@@ -503,10 +615,7 @@ def run_serve(args):
         return e0.elapsed_time(e1) / 1e3, st[0]["sweeps"]
 
     def admit(k):
-        budget = torch.cuda.mem_get_info()[0] + g.state_bytes(kmax)  # workspace is reused once held
-        while k > 1 and g.state_bytes(k) > budget:
-            k //= 2
-        return k
+        return admit_batch(k, torch.cuda.mem_get_info()[0], g.workspace_bytes(), g.state_bytes)
 
     def peak(model, seed, batches=3):
         srcs = gen.sources(n, kmax * batches, seed=seed)
@@ -534,7 +643,7 @@ def run_serve(args):
         srcs = gen.sources(n, nreq, seed=seed)
         queue = collections.deque()
         lat = np.zeros(nreq)
-        t_free, i, done = 0.0, 0, 0
+        t_free, i, done, refused = 0.0, 0, 0, 0
         while done < nreq:
             while i < nreq and arrivals[i] <= t_free:
                 queue.append(i)
@@ -543,6 +652,13 @@ def run_serve(args):
                 t_free = arrivals[i]
                 continue
             k = admit(min(kmax, len(queue)))
+            if k == 0:
+                # not even one source fits: the queued requests are refused
+                while queue:
+                    lat[queue.popleft()] = np.nan
+                    refused += 1
+                    done += 1
+                continue
             batch = [queue.popleft() for _ in range(k)]
             d, _ = run_batch(srcs[batch], model)
             t_free += d
@@ -550,8 +666,10 @@ def run_serve(args):
                 lat[j] = t_free - arrivals[j]
             done += k
         span = t_free - arrivals[0]
-        return {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                "queries_per_s": nreq / span}
+        ok = lat[~np.isnan(lat)]
+        return {"p50_ms": 1e3 * float(np.percentile(ok, 50)) if len(ok) else None,
+                "p99_ms": 1e3 * float(np.percentile(ok, 99)) if len(ok) else None,
+                "queries_per_s": len(ok) / span if span > 0 else None, "refused": refused}
 
     load = []
     for frac in (0.5, 0.8):
@@ -630,6 +748,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true", help="omit the oracle CPU baseline")
     ap.add_argument("--skip-warm", action="store_true", help="omit the learned warm-start comparison")
     ap.add_argument("--no-autotune", action="store_true", help="use the workload's fixed k-tile and the default switch")
+    ap.add_argument("--skip-side", action="store_true",
+                    help="omit the R-MAT-22 and small-graph records of the default run")
     ap.add_argument("--serve-scale", type=int, default=25, help="R-MAT scale of the serving workload")
     ap.add_argument("--serve-ef", type=int, default=32)
     ap.add_argument("--serve-train", type=int, default=2048)

@@ -55,6 +55,13 @@ typedef enum {
                               switch_edges that no level reaches, the call is FIFO-FwdPush
                               (Algorithm 2) by levels on the GPU */
 #define PPR_FLAG_FP32_ONLY 32 /* HP: correction passes with FP32 z_e only (no BF16 stage) */
+#define PPR_FLAG_TMA_GATHER 64 /* HP: in the FP32 correction passes of 64-source tiles, two
+                              warps of each block gather the rows with more than 16 in-edges
+                              by TMA (four-row tile::gather4 copies into shared memory) while
+                              the other warps take the light rows with vector loads.  Same
+                              answers; on R-MAT graphs slower than the default, where every
+                              warp gathers with per-lane 16-byte loads (0.54 against 0.33 ms
+                              per pass at scale 20, 2.2 against 1.5 ms at scale 22) */
 #define PPR_FLAG_FIXED_PASSES 8 /* HP: every pass in Q1.63.  By default the dense phase
                               solves for the remaining error e = pi - X with BF16 and FP32 passes,
                               folds e into the Q1.63 estimate X and certifies with one
@@ -203,10 +210,30 @@ ppr_status ppr_sssp_query_noalloc(ppr_graph* g, const int32_t* src, int32_t k, d
                                   double* out_pi, int32_t* out_sweeps, void* cuda_stream);
 
 /* Device bytes the workspace of a high-precision query of k sources needs
- * (k_tile as in ppr_query_opts, 0 = auto); the library reuses the workspace
- * across calls, so a server can admit a batch when this fits in free memory
- * plus what the graph already holds.  -1 on bad arguments. */
+ * (k_tile as in ppr_query_opts, 0 = the width the query would pick: the
+ * autotuned one of k's bucket, else the smallest power of two >= k up to 64),
+ * for alpha = 0.2 and lambda = 1e-8 (other values change only the per-pass
+ * residual sums, 512 bytes per pass), outputs in device or page-locked host
+ * memory (pageable host outputs add k x n x 8 bytes of staging each).  The
+ * library reuses the workspace across calls, so a server can admit a batch
+ * when this fits in free memory plus what the graph already holds
+ * (ppr_workspace_bytes); ppr_sssp_query applies the same test and refuses
+ * with PPR_ERR_ADMIT before any launch.  -1 on bad arguments. */
 int64_t ppr_query_state_bytes(const ppr_graph* g, int32_t k, int32_t k_tile);
+
+/* Device bytes the graph's query workspace holds now (it grows to the largest
+ * batch seen and is reused; ppr_free releases it).  -1 for a NULL graph. */
+int64_t ppr_workspace_bytes(const ppr_graph* g);
+
+/* Test hooks for the error paths, process-wide, off by default; no GPU fault
+ * is involved.  PPR_INJECT_FREE_BYTES: admission tests see at most `value`
+ * free device bytes (value < 0: off).  PPR_INJECT_ALLOC_FAIL: the value-th
+ * workspace allocation from now on fails as out of memory, and the call that
+ * made it returns PPR_ERR_OOM (value <= 0: off).  PPR_ERR_ARG for an unknown
+ * hook. */
+#define PPR_INJECT_FREE_BYTES 1
+#define PPR_INJECT_ALLOC_FAIL 2
+ppr_status ppr_inject(int32_t hook, int64_t value);
 
 /*
  * Measure, on a calibration batch src[k], every tile width up to the smallest

@@ -23,6 +23,9 @@ PPR_FLAG_INDEX = 4
 PPR_FLAG_FIXED_PASSES = 8
 PPR_FLAG_NO_ACTIVE = 16
 PPR_FLAG_FP32_ONLY = 32
+PPR_FLAG_TMA_GATHER = 64
+PPR_INJECT_FREE_BYTES = 1
+PPR_INJECT_ALLOC_FAIL = 2
 
 STATUS_NAMES = {0: "PPR_OK", -1: "PPR_ERR_ARG", -2: "PPR_ERR_GRAPH", -3: "PPR_ERR_OOM",
                 -4: "PPR_ERR_NOT_CONVERGED", -5: "PPR_ERR_CUDA", -6: "PPR_ERR_ADMIT"}
@@ -108,6 +111,8 @@ SIGNATURES = {
     "ppr_graph_n": (ctypes.c_int64, [_P]),
     "ppr_graph_m": (ctypes.c_int64, [_P]),
     "ppr_query_state_bytes": (ctypes.c_int64, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "ppr_workspace_bytes": (ctypes.c_int64, [_P]),
+    "ppr_inject": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64]),
     "ppr_index_build": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double, _P]),
     "ppr_index_get": (ctypes.c_int, [_P, _P]),
     "ppr_autotune": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(ppr_query_opts), _P,
@@ -251,6 +256,13 @@ def ppr_sssp_query_noalloc(graph: int, src, out_pi, alpha: float = 0.2, lam: flo
     return sweeps
 
 
+def ppr_inject(hook: int, value: int):
+    """Test hook for the error paths (see include/ppr.h): PPR_INJECT_FREE_BYTES
+    caps the free device bytes admission sees (value < 0: off);
+    PPR_INJECT_ALLOC_FAIL makes the value-th workspace allocation fail (0: off)."""
+    _check(load_library().ppr_inject(hook, value))
+
+
 def ppr_free(graph: int):
     if graph:
         load_library().ppr_free(graph)
@@ -300,6 +312,10 @@ class Graph:
     def state_bytes(self, k: int, k_tile: int = 0) -> int:
         """Device workspace of a high-precision query of k sources."""
         return load_library().ppr_query_state_bytes(self.handle, k, k_tile)
+
+    def workspace_bytes(self) -> int:
+        """Device bytes the graph's query workspace holds now."""
+        return load_library().ppr_workspace_bytes(self.handle)
 
     def query(self, src, mode: int = PPR_HP, out_pi=None, out_r=None, out_walk_counts=None, stream=None,
               warm_start=None, **opts):

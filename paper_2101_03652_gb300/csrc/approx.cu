@@ -366,6 +366,7 @@ static ppr_status run_approx(ppr_graph* g, const int32_t* src, int32_t k, const 
   {
     size_t free_b = 0, total_b = 0;
     PPR_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    free_b = admission_free_bytes(free_b);
     size_t have = ws.walk_a.bytes + ws.walk_b.bytes + ws.walk_c.bytes + ws.stage.bytes + ws.heavy_acc.bytes;
     if (need > free_b + have) {
       set_error("admission refused: approximate batch needs %zu bytes, %zu free", need, free_b);
@@ -383,12 +384,12 @@ static ppr_status run_approx(ppr_graph* g, const int32_t* src, int32_t k, const 
   PPR_TRY(ws.walk_c.ensure((size_t)KT * nscan * 8 + 4096));          // scan sums, counters
   const size_t acc_bytes = std::max<size_t>((size_t)plan->n_split * KT * 4, 4);
   const size_t cnt_bytes = std::max<size_t>((size_t)plan->n_split * 4, 4);
-  const bool fresh = ws.heavy_acc.bytes < acc_bytes || ws.heavy_cnt.bytes < cnt_bytes;
   PPR_TRY(ws.heavy_acc.ensure(std::max(acc_bytes, ws.heavy_acc.bytes)));
   PPR_TRY(ws.heavy_cnt.ensure(std::max(cnt_bytes, ws.heavy_cnt.bytes)));
-  if (fresh) {
+  if (ws.heavy_acc.fresh || ws.heavy_cnt.fresh) {
     PPR_CUDA_TRY(cudaMemsetAsync(ws.heavy_acc.ptr, 0, ws.heavy_acc.bytes, st));
     PPR_CUDA_TRY(cudaMemsetAsync(ws.heavy_cnt.ptr, 0, ws.heavy_cnt.bytes, st));
+    ws.heavy_acc.fresh = ws.heavy_cnt.fresh = false;
   }
   if (stage) PPR_TRY(ws.stage.ensure(stage));
   PPR_TRY(ws.counters.ensure(8192));

@@ -10,6 +10,7 @@
 // the most frequently gathered nodes (in R-MAT, in- and out-degree are
 // strongly correlated) occupy a small, cache-friendly id range.
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -33,10 +34,23 @@ void set_error(const char* fmt, ...) {
 void clear_error() { g_last_error.clear(); }
 const char* last_error_cstr() { return g_last_error.c_str(); }
 
+static std::atomic<int64_t> g_inject_free{-1};
+static std::atomic<int64_t> g_inject_alloc{0};
+
+int64_t injected_free_cap() { return g_inject_free.load(); }
+size_t admission_free_bytes(size_t free_bytes) {
+  const int64_t cap = g_inject_free.load();
+  return cap >= 0 ? std::min(free_bytes, (size_t)cap) : free_bytes;
+}
+
 ppr_status DevBuf::ensure(size_t want) {
   if (want <= bytes && ptr) return PPR_OK;
   release();
   if (want == 0) return PPR_OK;
+  if (g_inject_alloc.load() > 0 && g_inject_alloc.fetch_sub(1) == 1) {
+    set_error("device allocation of %zu bytes failed: injected allocation failure", want);
+    return PPR_ERR_OOM;
+  }
   cudaError_t e = cudaMalloc(&ptr, want);
   if (e != cudaSuccess) {
     ptr = nullptr;
@@ -46,6 +60,7 @@ ppr_status DevBuf::ensure(size_t want) {
     return PPR_ERR_OOM;
   }
   bytes = want;
+  fresh = true;
   return PPR_OK;
 }
 void DevBuf::release() {
@@ -53,9 +68,25 @@ void DevBuf::release() {
   ptr = nullptr;
   bytes = 0;
 }
+size_t Workspace::device_bytes() const {
+  size_t b = 0;
+  for (const DevBuf* d : {&r, &pi, &za, &zb, &stamp, &front_a, &front_b, &ent_share, &ent_rem, &chunks, &heavy_acc,
+                          &heavy_cnt, &counters, &resid, &status, &stage, &walk_a, &walk_b, &walk_c})
+    b += d->bytes;
+  return b;
+}
+
+size_t Workspace::hp_bytes() const {
+  size_t b = 0;
+  for (const DevBuf* d : {&r, &pi, &za, &zb, &stamp, &front_a, &front_b, &ent_share, &ent_rem, &chunks, &heavy_acc,
+                          &heavy_cnt, &counters, &resid, &status, &stage})
+    b += d->bytes;
+  return b;
+}
+
 void Workspace::release() {
   for (DevBuf* b : {&r, &pi, &za, &zb, &stamp, &front_a, &front_b, &ent_share, &ent_rem, &chunks, &heavy_acc,
-                    &heavy_cnt, &counters, &resid, &stage, &walk_a, &walk_b, &walk_c})
+                    &heavy_cnt, &counters, &resid, &status, &stage, &walk_a, &walk_b, &walk_c})
     b->release();
   if (pinned) cudaFreeHost(pinned);
   pinned = nullptr;
@@ -158,6 +189,9 @@ static void free_graph_arrays(ppr_graph* g) {
     if (pl.d_items) cudaFree(pl.d_items);
     if (pl.d_npieces) cudaFree(pl.d_npieces);
   }
+  for (void* p : {(void*)g->tma.d_chunks, (void*)g->tma.d_split_slot, (void*)g->tma.d_split_np,
+                  (void*)g->tma.d_split_acc, (void*)g->tma.d_split_cnt})
+    if (p) cudaFree(p);
 }
 
 static ppr_status build_and_upload(ppr_graph* g, const int64_t* rp, const int32_t* ci, cudaStream_t st) {
@@ -291,6 +325,22 @@ void ppr_free(ppr_graph* g) {
   g->ws.release();
   delete g;
 }
+
+ppr_status ppr_inject(int32_t hook, int64_t value) {
+  clear_error();
+  if (hook == PPR_INJECT_FREE_BYTES) {
+    g_inject_free.store(value < 0 ? -1 : value);
+    return PPR_OK;
+  }
+  if (hook == PPR_INJECT_ALLOC_FAIL) {
+    g_inject_alloc.store(value < 0 ? 0 : value);
+    return PPR_OK;
+  }
+  set_error("unknown injection hook %d", hook);
+  return PPR_ERR_ARG;
+}
+
+int64_t ppr_workspace_bytes(const ppr_graph* g) { return g ? (int64_t)g->ws.device_bytes() : -1; }
 
 int64_t ppr_graph_n(const ppr_graph* g) { return g ? g->n : 0; }
 int64_t ppr_graph_m(const ppr_graph* g) { return g ? g->m : 0; }

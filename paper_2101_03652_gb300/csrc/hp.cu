@@ -40,6 +40,9 @@
 #include "sweep_kernel.cuh"
 #include "epoch_kernel.cuh"
 #include "refine_kernel.cuh"
+#include "refine_tma_kernel.cuh"
+
+#include <cudaTypedefs.h>
 
 namespace ppr {
 
@@ -300,6 +303,8 @@ static ppr_status build_plan(ppr_graph* g, int kt, Plan& p, cudaStream_t st) {
     }
     items.push_back(make_int4(1, u0, u, 0));
   }
+  p.n_items_heavy = (int32_t)items.size();
+  p.u_light = u;
   while (u < n && d[u] > 0) {
     int32_t u0 = u;
     int cost = 0;
@@ -424,6 +429,7 @@ struct RefineTile {
   const int32_t* src_new = nullptr;
   u64* mass = nullptr;       // [KT] device scratch for exact column sums
   bool fp32_only = false;    // no BF16 stage
+  bool tma_gather = false;   // 64-source FP32 passes with TMA gathers of the heavy rows
 };
 
 constexpr float kRelax = 1.15f;  // over-relaxation of in-place correction passes
@@ -449,6 +455,112 @@ static ppr_status refine_kernel_setup(ppr_graph* g, Plan** plan, int* grid, int*
   PPR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, refine_pass_kernel<KT, T, false>, 256, 0));
   *grid = sm_count() * std::max(bps, 1);
   PPR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, refine_pass_kernel<KT, T, true>, 256, 0));
+  *grid_meas = sm_count() * std::max(bps, 1);
+  return PPR_OK;
+}
+
+// ------------------------------------------------------------ TMA passes
+constexpr int kTmaWarps = 2;  // TMA warps per block of the 64-source FP32 pass (the rest take light rows)
+
+// Chunks of the TMA pass over rows [0, u_h) of the 64-source FP32 work list:
+// chunk c holds edges [c kTmaChunk, (c+1) kTmaChunk); a row meeting two or
+// more chunks gets a slot for its partial sums.  Built once per graph.
+static ppr_status get_tma_plan(ppr_graph* g, const Plan& lsu_plan, ppr_graph::TmaPlan** out, cudaStream_t st) {
+  ppr_graph::TmaPlan& t = g->tma;
+  if (!t.built) {
+    const std::vector<int32_t>& d = g->h_in_deg_sorted;
+    t.u_h = lsu_plan.u_light;
+    t.item0 = lsu_plan.n_items_heavy;
+    int64_t h = 0;
+    for (int32_t u = 0; u < t.u_h; ++u) h += d[u];
+    t.h_edges = (int32_t)h;
+    t.n_chunks = (int32_t)((h + kTmaChunk - 1) / kTmaChunk);
+    std::vector<int4> chunks((size_t)std::max(t.n_chunks, 1));
+    std::vector<int32_t> slot((size_t)std::max(t.u_h, 1), -1), np;
+    int64_t rs = 0;
+    int32_t c = 0;
+    for (int32_t u = 0; u < t.u_h; ++u) {
+      const int64_t re = rs + d[u];
+      for (; c < t.n_chunks && (int64_t)c * kTmaChunk < re; ++c)
+        chunks[c] = make_int4(u, (int)rs, (int)re, 0);
+      const int64_t c0 = rs / kTmaChunk, c1 = (re - 1) / kTmaChunk;
+      if (c1 > c0) {
+        slot[u] = (int32_t)np.size();
+        np.push_back((int32_t)(c1 - c0 + 1));
+      }
+      rs = re;
+    }
+    t.n_slots = (int32_t)np.size();
+    PPR_CUDA_TRY(cudaMalloc((void**)&t.d_chunks, sizeof(int4) * chunks.size()));
+    PPR_CUDA_TRY(cudaMemcpyAsync(t.d_chunks, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice, st));
+    PPR_CUDA_TRY(cudaMalloc((void**)&t.d_split_slot, sizeof(int32_t) * slot.size()));
+    PPR_CUDA_TRY(
+        cudaMemcpyAsync(t.d_split_slot, slot.data(), sizeof(int32_t) * slot.size(), cudaMemcpyHostToDevice, st));
+    const size_t ns = (size_t)std::max(t.n_slots, 1);
+    np.resize(ns, 1);
+    PPR_CUDA_TRY(cudaMalloc((void**)&t.d_split_np, sizeof(int32_t) * ns));
+    PPR_CUDA_TRY(cudaMemcpyAsync(t.d_split_np, np.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, st));
+    PPR_CUDA_TRY(cudaMalloc((void**)&t.d_split_acc, sizeof(float) * 64 * ns));
+    PPR_CUDA_TRY(cudaMemsetAsync(t.d_split_acc, 0, sizeof(float) * 64 * ns, st));
+    PPR_CUDA_TRY(cudaMalloc((void**)&t.d_split_cnt, sizeof(unsigned int) * ns));
+    PPR_CUDA_TRY(cudaMemsetAsync(t.d_split_cnt, 0, sizeof(unsigned int) * ns, st));
+    PPR_CUDA_TRY(cudaStreamSynchronize(st));
+    t.built = true;
+  }
+  *out = &t;
+  return PPR_OK;
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      (void)cudaGetLastError();
+  }
+  return fn;
+}
+
+// an n x 64 FP32 tile (rows of 256 B) as a 2-D tensor with one-row boxes, the
+// layout tile::gather4 copies from
+static ppr_status encode_tile_map(CUtensorMap* map, const void* base, int64_t n) {
+  auto enc = tensor_map_encoder();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return PPR_ERR_CUDA;
+  }
+  const cuuint64_t dims[2] = {64, (cuuint64_t)n};
+  const cuuint64_t strides[1] = {64 * sizeof(float)};
+  const cuuint32_t box[2] = {64, 1};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return PPR_ERR_CUDA;
+  }
+  return PPR_OK;
+}
+
+// grids of the TMA pass (unmeasured, measured): one full wave of resident blocks
+static ppr_status tma_kernel_grids(int* grid, int* grid_meas) {
+  const size_t smem = tma_smem_bytes(kTmaWarps);
+  auto k0 = refine_tma_kernel<false, kTmaWarps>;
+  auto k1 = refine_tma_kernel<true, kTmaWarps>;
+  PPR_CUDA_TRY(cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  PPR_CUDA_TRY(cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int bps = 0;
+  PPR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k0, 256, smem));
+  *grid = sm_count() * std::max(bps, 1);
+  PPR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k1, 256, smem));
   *grid_meas = sm_count() * std::max(bps, 1);
   return PPR_OK;
 }
@@ -485,6 +597,34 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
   ra.heavy_acc = ws.heavy_acc.as<float>();
   ra.heavy_cnt = ws.heavy_cnt.as<unsigned int>();
   const bool use_bf16 = !t.fp32_only;
+
+  // FP32 passes of a 64-source tile with PPR_FLAG_TMA_GATHER: rows with many
+  // in-edges gathered by TMA
+  bool use_tma = false;
+  TmaArgs ta{};
+  CUtensorMap maps[2];
+  int grid_tma = 0, grid_tma_meas = 0;
+  if constexpr (KT == 64) {
+    ppr_graph::TmaPlan* tp = nullptr;
+    if (t.tma_gather) PPR_TRY(get_tma_plan(g, *plans[1], &tp, st));
+    if (tp && tp->n_chunks > 0) {
+      PPR_TRY(encode_tile_map(&maps[0], zbuf_a, n));
+      PPR_TRY(encode_tile_map(&maps[1], zbuf_b, n));
+      PPR_TRY(tma_kernel_grids(&grid_tma, &grid_tma_meas));
+      ta.h_edges = tp->h_edges;
+      ta.u_h = tp->u_h;
+      ta.n_chunks = tp->n_chunks;
+      ta.item0 = tp->item0;
+      ta.chunks = tp->d_chunks;
+      ta.split_slot = tp->d_split_slot;
+      ta.split_np = tp->d_split_np;
+      ta.split_acc = tp->d_split_acc;
+      ta.split_cnt = tp->d_split_cnt;
+      ta.status = ws.status.as<unsigned int>();
+      use_tma = true;
+    }
+  }
+  unsigned int* h_status = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(hpin) + 64 * 8);
 
   const double slack = (double)m * 0.5 / kFixOne / alpha;
   // goal of the correction passes: after the fold the exact pass measures
@@ -585,6 +725,12 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
         if (prec == 0) {
           if (last) refine_pass_kernel<KT, bf16, true><<<grids_meas[0], 256, 0, st>>>(ra);
           else refine_pass_kernel<KT, bf16, false><<<grids[0], 256, 0, st>>>(ra);
+        } else if (use_tma) {
+          ta.map = zcur == zbuf_a ? maps[0] : maps[1];
+          if (last)
+            refine_tma_kernel<true, kTmaWarps><<<grid_tma_meas, 256, tma_smem_bytes(kTmaWarps), st>>>(ra, ta);
+          else
+            refine_tma_kernel<false, kTmaWarps><<<grid_tma, 256, tma_smem_bytes(kTmaWarps), st>>>(ra, ta);
         } else {
           if (last) refine_pass_kernel<KT, float, true><<<grids_meas[1], 256, 0, st>>>(ra);
           else refine_pass_kernel<KT, float, false><<<grids[1], 256, 0, st>>>(ra);
@@ -598,7 +744,12 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
       ro.passes[prec] += S;
       launches += S;
       PPR_CUDA_TRY(cudaMemcpyAsync(hpin, resid, 64 * 8, cudaMemcpyDeviceToHost, st));
+      if (use_tma) PPR_CUDA_TRY(cudaMemcpyAsync(h_status, ta.status, 4, cudaMemcpyDeviceToHost, st));
       PPR_CUDA_TRY(cudaStreamSynchronize(st));
+      if (use_tma && *h_status) {
+        set_error("a TMA row-gather wait timed out in a correction pass");
+        return PPR_ERR_CUDA;
+      }
       float a_ms = 0.f;
       cudaEventElapsedTime(&a_ms, es0, es1);
       ms_sweep += a_ms;
@@ -748,22 +899,21 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
     return PPR_ERR_ARG;
   }
 
-  // admission: state for one tile plus staging of host outputs
-  size_t need = 4 * cells * 8 + cells * 4 * 4 + cells * 16 + (size_t)m * KT / kPushChunk * 8 + (size_t)max_sweeps * KT * 8;
+  // admission: state for one tile plus staging of host outputs, against free
+  // device memory plus what the workspace already holds (reused)
+  const size_t need = hp_workspace_bytes(g, KT, max_sweeps);
   size_t stage_bytes = 0;
   if (pi_on_host) stage_bytes += (size_t)k * n * 8;
   if (r_on_host) stage_bytes += (size_t)k * n * 8;
   {
-    size_t have_bytes = ws.r.bytes + ws.pi.bytes + ws.za.bytes + ws.zb.bytes + ws.stamp.bytes + ws.front_a.bytes +
-                        ws.front_b.bytes + ws.heavy_acc.bytes + ws.resid.bytes + ws.stage.bytes;
     size_t free_b = 0, total_b = 0;
     PPR_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-    if (need + stage_bytes > free_b + have_bytes) {
+    free_b = admission_free_bytes(free_b);
+    if (need + stage_bytes > free_b + ws.hp_bytes()) {
       set_error("admission refused: batch state needs %zu bytes, %zu free", need + stage_bytes, free_b);
       return PPR_ERR_ADMIT;
     }
   }
-  bool fresh_stamp = ws.stamp.bytes < cells * 4;
   PPR_TRY(ws.r.ensure(cells * 8));
   PPR_TRY(ws.pi.ensure(cells * 8));
   PPR_TRY(ws.za.ensure(cells * 8));
@@ -780,24 +930,29 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
   Plan& plan = *plan_p;
   const size_t acc_bytes = std::max<size_t>((size_t)plan.n_split * KT * 8, 8);
   const size_t cnt_bytes = std::max<size_t>((size_t)plan.n_split * 4, 4);
-  bool fresh_heavy = ws.heavy_acc.bytes < acc_bytes || ws.heavy_cnt.bytes < cnt_bytes;
   PPR_TRY(ws.heavy_acc.ensure(acc_bytes));
   PPR_TRY(ws.heavy_cnt.ensure(cnt_bytes));
   PPR_TRY(ws.counters.ensure(16384));
   PPR_TRY(ws.resid.ensure((size_t)(max_sweeps + 1) * 64 * 8));
+  PPR_TRY(ws.status.ensure(8));
+  PPR_CUDA_TRY(cudaMemsetAsync(ws.status.ptr, 0, 8, st));
 
   if (stage_bytes) PPR_TRY(ws.stage.ensure(stage_bytes));
   if (!ws.pinned) {
     PPR_CUDA_TRY(cudaMallocHost(&ws.pinned, 65536));
     ws.pinned_bytes = 65536;
   }
-  if (fresh_stamp || g->stamp_epoch > 0xF0000000u) {
+  // buffers whose contents must start at zero, cleared once after each
+  // (re)allocation (also when an earlier call failed before clearing them)
+  if (ws.stamp.fresh || g->stamp_epoch > 0xF0000000u) {
     PPR_CUDA_TRY(cudaMemsetAsync(ws.stamp.ptr, 0, ws.stamp.bytes, st));
     g->stamp_epoch = 0;
+    ws.stamp.fresh = false;
   }
-  if (fresh_heavy) {
+  if (ws.heavy_acc.fresh || ws.heavy_cnt.fresh) {
     PPR_CUDA_TRY(cudaMemsetAsync(ws.heavy_acc.ptr, 0, ws.heavy_acc.bytes, st));
     PPR_CUDA_TRY(cudaMemsetAsync(ws.heavy_cnt.ptr, 0, ws.heavy_cnt.bytes, st));
+    ws.heavy_acc.fresh = ws.heavy_cnt.fresh = false;
   }
   PPR_TRY(ensure_alpha(g, alpha, st));
 
@@ -984,6 +1139,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
       rt.src_new = src_new;
       rt.mass = mass;
       rt.fp32_only = (o.flags & PPR_FLAG_FP32_ONLY) != 0;
+      rt.tma_gather = (o.flags & PPR_FLAG_TMA_GATHER) != 0;
       RefineOut ro;
       status = run_refine<KT>(g, plan, sweep_grid, grid_ew, sa, rt, resid, hpin, sweeps, launches, bound, r0,
                               ms_sweep, ro, es0, es1, st);
@@ -1192,26 +1348,44 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
 
 // device bytes a high-precision query of k sources allocates (workspace for one
 // tile), as used by the admission check of run_hp (host staging excluded)
-int64_t hp_state_bytes(const ppr_graph* g, int32_t k, int32_t kt) {
+// tile width of an HP query of k sources: the caller's, else the autotuned
+// one of k's bucket, else the smallest power of two >= k (at most 64): one
+// pass per tile, and a wider tile costs less per source than two narrow ones
+int hp_tile_width(const ppr_graph* g, int32_t k, int32_t k_tile) {
+  int kt = k_tile;
+  if (kt == 0 && g->tuned_kt[tune_bucket(k)] > 0) kt = g->tuned_kt[tune_bucket(k)];
   if (kt == 0) {
     kt = 1;
     while (kt < k && kt < 64) kt <<= 1;
   }
+  return kt;
+}
+
+// Device bytes run_hp<kt> holds in the graph's workspace (staging of outputs
+// to pageable host memory excluded): the four Q1.63 tile arrays, frontier
+// stamps and lists and the per-entry push remainders (4 x 4 B per cell), the
+// per-entry shares and the push chunk records, the partial sums of split rows
+// (rows longer than one piece of the Q1.63 work list, which splits the most
+// rows), counters, the per-pass residual sums and the status word.
+size_t hp_workspace_bytes(const ppr_graph* g, int kt, int max_sweeps) {
   const size_t cells = (size_t)g->n * kt;
-  const int max_sweeps = 4 * 83 + 64;
-  return (int64_t)(4 * cells * 8 + cells * 4 * 4 + cells * 16 + (size_t)g->m * kt / kPushChunk * 8 +
-                   (size_t)max_sweeps * kt * 8);
+  const int L = kt >= 2 ? kt / 2 : 1;  // lanes per row of the Q1.63 passes
+  const int piece = std::max(kItemPeriods * (32 / L) * kUnr, 256);
+  const std::vector<int32_t>& d = g->h_in_deg_sorted;
+  size_t n_split = 0;
+  while (n_split < d.size() && d[n_split] > piece) ++n_split;
+  return 4 * cells * 8 + 4 * cells * 4 + cells * 8 + (cells + (size_t)g->m * kt / kPushChunk + 64) * 8 +
+         std::max<size_t>(n_split * kt * 8, 8) + std::max<size_t>(n_split * 4, 4) + 16384 +
+         (size_t)(max_sweeps + 1) * 64 * 8 + 8;
+}
+
+int64_t hp_state_bytes(const ppr_graph* g, int32_t k, int32_t kt) {
+  return (int64_t)hp_workspace_bytes(g, hp_tile_width(g, k, kt), sweep_limit(0.2, 1e-8));
 }
 
 ppr_status query_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query_opts& o, double* out_pi,
                     double* out_r, ppr_stats* stats, cudaStream_t st) {
-  int kt = o.k_tile;
-  if (kt == 0 && g->tuned_kt[tune_bucket(k)] > 0) kt = g->tuned_kt[tune_bucket(k)];
-  if (kt == 0) {
-    // one pass per tile: a wider tile costs less per source than two narrow ones
-    kt = 1;
-    while (kt < k && kt < 64) kt <<= 1;
-  }
+  const int kt = hp_tile_width(g, k, o.k_tile);
   if ((size_t)g->n * kt >= ((size_t)1 << 32)) {
     set_error("n * k_tile must stay below 2^32");
     return PPR_ERR_ARG;

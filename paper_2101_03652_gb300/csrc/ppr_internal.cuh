@@ -59,11 +59,18 @@ constexpr uint64_t kFixOneRaw = 0x8000000000000000ull;
 struct DevBuf {
   void* ptr = nullptr;
   size_t bytes = 0;
+  bool fresh = false;  // newly allocated, contents undefined (the user clears it once initialised)
   ppr_status ensure(size_t want);
   void release();
   template <class T>
   T* as() const { return static_cast<T*>(ptr); }
 };
+
+// Host-side fault injection for the tests of the error paths (ppr_inject):
+// a cap on the free device bytes the admission checks see (< 0: off), and a
+// countdown after which a workspace allocation fails as out of memory (<= 0: off).
+int64_t injected_free_cap();
+size_t admission_free_bytes(size_t free_bytes);
 
 struct Workspace {
   DevBuf r, pi, za, zb;          // n*KT uint64 each (HP): residue, reserve, ping-pong z
@@ -74,11 +81,14 @@ struct Workspace {
   DevBuf heavy_acc, heavy_cnt;   // partial sums of split rows
   DevBuf counters;               // small device counters
   DevBuf resid;                  // per-sweep per-column residual sums (double)
+  DevBuf status;                 // device status word of the TMA passes (timed-out waits)
   DevBuf stage;                  // device staging for host outputs
   DevBuf walk_a, walk_b, walk_c; // APPROX path buffers
   void* pinned = nullptr;        // small pinned host buffer for readbacks
   size_t pinned_bytes = 0;
   void release();
+  size_t device_bytes() const;   // device bytes held by all buffers above
+  size_t hp_bytes() const;       // the part a high-precision query reuses
 };
 
 }  // namespace ppr
@@ -120,9 +130,21 @@ struct ppr_graph {
     int kt = 0;
     int32_t n_items_all = 0, n_items_nz = 0;
     int32_t n_split = 0;          // rows cut into pieces (the first n_split rows)
+    int32_t n_items_heavy = 0;    // items before the first light-row item
+    int32_t u_light = 0;          // first row with at most kLightMax in-edges
     int4* d_items = nullptr;
     int32_t* d_npieces = nullptr; // pieces per split row
   } plans[7];
+  // chunks of the TMA correction passes (rows [0, u_h), edges [0, h_edges))
+  struct TmaPlan {
+    bool built = false;
+    int32_t u_h = 0, h_edges = 0, n_chunks = 0, n_slots = 0, item0 = 0;
+    int4* d_chunks = nullptr;         // per chunk: {row of its first edge, row start, row end, 0}
+    int32_t* d_split_slot = nullptr;  // per row < u_h: slot of a row meeting two or more chunks, else -1
+    int32_t* d_split_np = nullptr;    // per slot: chunks the row meets
+    float* d_split_acc = nullptr;     // per slot: 64 partial sums
+    unsigned int* d_split_cnt = nullptr;
+  } tma;
   ppr::Workspace ws;
 };
 
@@ -141,6 +163,8 @@ ppr_status warm_start_tile(const void* model, ppr_graph* g, const int32_t* src_n
                            unsigned long long* z0, unsigned long long* x0, cudaStream_t st);
 int warm_correction_passes(const void* model);
 int64_t hp_state_bytes(const ppr_graph* g, int32_t k, int32_t kt);
+int hp_tile_width(const ppr_graph* g, int32_t k, int32_t k_tile);
+size_t hp_workspace_bytes(const ppr_graph* g, int kt, int max_sweeps);
 int tune_bucket(int32_t k);
 // x + mu q with mu = 1 - sum x: z of it, and the corrected x when x_out is not NULL
 ppr_status warm_correct_tile(const void* model, ppr_graph* g, const int32_t* src_new, int ncols, int kt, double alpha,

@@ -266,68 +266,87 @@ __device__ __forceinline__ void refine_gather_warp(const RefArgs& a, int e_begin
   }
 }
 
+// One work item of a pass (see build_plan): a piece of a split row, a run of
+// medium rows (a warp per row) or a run of light rows (L lanes per row).
+template <int KT, typename T, bool MEAS>
+__device__ __forceinline__ void refine_item(const RefArgs& a, const int4 w, int lane, int slot,
+                                            float (&res)[RLay<KT, T>::V]) {
+  constexpr int V = RLay<KT, T>::V, L = RLay<KT, T>::L;
+  const T* z = static_cast<const T*>(a.ze_in);
+  if (w.x == 0) {
+    // piece of a split row; the last piece to arrive finishes the row
+    const int u = w.y;
+    float acc[V] = {};
+    refine_gather_warp<KT, T, !MEAS>(a, w.z, w.w, lane, slot, acc);
+#pragma unroll
+    for (int off = L; off < 32; off <<= 1)
+#pragma unroll
+      for (int q = 0; q < V; ++q) acc[q] += __shfl_xor_sync(kFull, acc[q], off);
+    if (lane < L)
+#pragma unroll
+      for (int q = 0; q < V; ++q) atomicAdd(&a.heavy_acc[(size_t)u * KT + slot * V + q], acc[q]);
+    __threadfence();
+    unsigned ticket = 0;
+    if (lane == 0) ticket = atomicAdd(&a.heavy_cnt[u], 1u);
+    ticket = __shfl_sync(kFull, ticket, 0);
+    if (ticket == (unsigned)a.npieces[u] - 1u) {
+      __threadfence();
+      if (lane < L) {
+        float tot[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) tot[q] = atomicExch(&a.heavy_acc[(size_t)u * KT + slot * V + q], 0.f);
+        refine_epilogue<KT, T, MEAS>(a, u, slot, refine_prefetch<KT, T>(a, u, slot), tot, res);
+      }
+      if (lane == 0) atomicExch(&a.heavy_cnt[u], 0u);
+    }
+  } else if (w.x == 1) {
+    for (int u = w.y; u < w.z; ++u) {
+      const auto pre = refine_prefetch<KT, T>(a, u, slot);
+      float acc[V] = {};
+      refine_gather_warp<KT, T, !MEAS>(a, __ldg(&a.in_rp[u]), __ldg(&a.in_rp[u + 1]), lane, slot, acc);
+#pragma unroll
+      for (int off = L; off < 32; off <<= 1)
+#pragma unroll
+        for (int q = 0; q < V; ++q) acc[q] += __shfl_xor_sync(kFull, acc[q], off);
+      if (lane < L) refine_epilogue<KT, T, MEAS>(a, u, slot, pre, acc, res);
+    }
+  } else {
+    for (int u = w.y + lane / L; u < w.z; u += 32 / L) {
+      const auto pre = refine_prefetch<KT, T>(a, u, slot);
+      const int e1 = __ldg(&a.in_rp[u + 1]);
+      float acc[V] = {};
+#pragma unroll RefTune<KT, T, MEAS>::UNR
+      for (int e = __ldg(&a.in_rp[u]); e < e1; ++e)
+        add_raw<T, V>(acc, ld_raw<T, V, !MEAS>(z + (size_t)__ldg(&a.in_ci[e]) * KT + slot * V));
+      refine_epilogue<KT, T, MEAS>(a, u, slot, pre, acc, res);
+    }
+  }
+}
+
+// per-column sums |e' - e| of a block into resid: warp w's partial sums are
+// in sred[w][0..KT), then one atomic per column
+template <int KT>
+__device__ __forceinline__ void refine_resid_block(float (&sred)[8][KT], double* resid) {
+  __syncthreads();
+  if (threadIdx.x < KT) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += (double)sred[w][threadIdx.x];
+    atomicAdd(&resid[threadIdx.x], sum);
+  }
+}
+
 // MEAS: the measured (synchronous) pass of a batch, which also sums |e' - e|
 template <int KT, typename T, bool MEAS>
 __global__ void __launch_bounds__(256, (RefTune<KT, T, MEAS>::MIN_BLOCKS)) refine_pass_kernel(RefArgs a) {
   constexpr int V = RLay<KT, T>::V, L = RLay<KT, T>::L;
   const int lane = threadIdx.x & 31;
   const int slot = lane % L;
-  const T* z = static_cast<const T*>(a.ze_in);
   float res[V];
 #pragma unroll
   for (int q = 0; q < V; ++q) res[q] = 0.f;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < a.n_items; it += nwarps) {
-    const int4 w = __ldg(&a.items[it]);
-    if (w.x == 0) {
-      // piece of a split row; the last piece to arrive finishes the row
-      const int u = w.y;
-      float acc[V] = {};
-      refine_gather_warp<KT, T, !MEAS>(a, w.z, w.w, lane, slot, acc);
-#pragma unroll
-      for (int off = L; off < 32; off <<= 1)
-#pragma unroll
-        for (int q = 0; q < V; ++q) acc[q] += __shfl_xor_sync(kFull, acc[q], off);
-      if (lane < L)
-#pragma unroll
-        for (int q = 0; q < V; ++q) atomicAdd(&a.heavy_acc[(size_t)u * KT + slot * V + q], acc[q]);
-      __threadfence();
-      unsigned ticket = 0;
-      if (lane == 0) ticket = atomicAdd(&a.heavy_cnt[u], 1u);
-      ticket = __shfl_sync(kFull, ticket, 0);
-      if (ticket == (unsigned)a.npieces[u] - 1u) {
-        __threadfence();
-        if (lane < L) {
-          float tot[V];
-#pragma unroll
-          for (int q = 0; q < V; ++q) tot[q] = atomicExch(&a.heavy_acc[(size_t)u * KT + slot * V + q], 0.f);
-          refine_epilogue<KT, T, MEAS>(a, u, slot, refine_prefetch<KT, T>(a, u, slot), tot, res);
-        }
-        if (lane == 0) atomicExch(&a.heavy_cnt[u], 0u);
-      }
-    } else if (w.x == 1) {
-      for (int u = w.y; u < w.z; ++u) {
-        const auto pre = refine_prefetch<KT, T>(a, u, slot);
-        float acc[V] = {};
-        refine_gather_warp<KT, T, !MEAS>(a, __ldg(&a.in_rp[u]), __ldg(&a.in_rp[u + 1]), lane, slot, acc);
-#pragma unroll
-        for (int off = L; off < 32; off <<= 1)
-#pragma unroll
-          for (int q = 0; q < V; ++q) acc[q] += __shfl_xor_sync(kFull, acc[q], off);
-        if (lane < L) refine_epilogue<KT, T, MEAS>(a, u, slot, pre, acc, res);
-      }
-    } else {
-      for (int u = w.y + lane / L; u < w.z; u += 32 / L) {
-        const auto pre = refine_prefetch<KT, T>(a, u, slot);
-        const int e1 = __ldg(&a.in_rp[u + 1]);
-        float acc[V] = {};
-#pragma unroll RefTune<KT, T, MEAS>::UNR
-        for (int e = __ldg(&a.in_rp[u]); e < e1; ++e)
-          add_raw<T, V>(acc, ld_raw<T, V, !MEAS>(z + (size_t)__ldg(&a.in_ci[e]) * KT + slot * V));
-        refine_epilogue<KT, T, MEAS>(a, u, slot, pre, acc, res);
-      }
-    }
-  }
+  for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < a.n_items; it += nwarps)
+    refine_item<KT, T, MEAS>(a, __ldg(&a.items[it]), lane, slot, res);
   if (!MEAS) return;
   __shared__ float sred[8][KT];
 #pragma unroll
@@ -338,12 +357,7 @@ __global__ void __launch_bounds__(256, (RefTune<KT, T, MEAS>::MIN_BLOCKS)) refin
   if (lane < L)
 #pragma unroll
     for (int q = 0; q < V; ++q) sred[warp][lane * V + q] = res[q];
-  __syncthreads();
-  if (threadIdx.x < KT) {
-    double sum = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += (double)sred[w][threadIdx.x];
-    atomicAdd(&a.resid[threadIdx.x], sum);
-  }
+  refine_resid_block<KT>(sred, a.resid);
 }
 
 // z_e of the BF16 passes into FP32 (exact) for the FP32 passes that follow

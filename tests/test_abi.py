@@ -86,6 +86,10 @@ def test_binding_constants_match_the_header():
     text = open(os.path.join(ROOT, "include", "ppr.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     defines = {k: int(v) for k, v in re.findall(r"#define\s+(PPR_FLAG_[A-Z0-9_]+)\s+(\d+)", text)}
+    hooks = {k: int(v) for k, v in re.findall(r"#define\s+(PPR_INJECT_[A-Z0-9_]+)\s+(\d+)", text)}
+    assert len(hooks) == 2
+    for name, value in hooks.items():
+        assert getattr(binding, name) == value, name
     enums = {k: int(v) for k, v in re.findall(r"\b(PPR_(?:OK|ERR_[A-Z_]+|HP|APPROX))\s*=\s*(-?\d+)", text)}
     assert len(defines) >= 6 and len(enums) >= 9
     for name, value in {**defines, **enums}.items():
@@ -213,3 +217,17 @@ def test_model_marshalling_checks_labels_and_outputs(monkeypatch):
         m.estimate([0, 1, 2], out=np.zeros((2, n)))
     assert len(fake.calls) == 2
     m.handle = None
+
+
+def test_injection_hooks_and_workspace_query_without_device():
+    """The error-path hooks are plain host state: set and cleared without a
+    device; an unknown hook is an argument error; a NULL graph holds no
+    workspace."""
+    lib = P.load_library()
+    assert lib.ppr_inject(binding.PPR_INJECT_FREE_BYTES, 1 << 20) == binding.PPR_OK
+    assert lib.ppr_inject(binding.PPR_INJECT_FREE_BYTES, -1) == binding.PPR_OK
+    assert lib.ppr_inject(binding.PPR_INJECT_ALLOC_FAIL, 3) == binding.PPR_OK
+    assert lib.ppr_inject(binding.PPR_INJECT_ALLOC_FAIL, 0) == binding.PPR_OK
+    assert lib.ppr_inject(99, 0) == binding.PPR_ERR_ARG
+    assert b"unknown injection hook" in lib.ppr_last_error()
+    assert lib.ppr_workspace_bytes(None) == -1

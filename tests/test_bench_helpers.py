@@ -57,3 +57,36 @@ def test_traffic_record_follows_the_kernel_source(monkeypatch, kernel, workload)
 
 def test_unknown_kernel_has_no_traffic():
     assert bench.ncu_traffic("rmat22-index", "index_query_kernel") is None
+
+
+def test_hp_roofline_entry():
+    """The dominant kernel is the FP32 pass when the query ran any (its bytes
+    over its average launch time), else the Q1.63 pass."""
+    r = bench.hp_roofline(N20, M20, 64, fp32_ms=33.26, fp32_launches=100, sweep_ms=5.0, sweep_launches=10,
+                          workload="none")
+    assert r["kernel"] == "refine_pass_kernel<64, float>"
+    assert abs(r["achieved"] - bench.fp32_pass_bytes(N20, M20, 64) / 0.3326e-3 / 1e9) < 1e-6
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert r["traffic"] is None                                       # no capture for this workload
+    r = bench.hp_roofline(N20, M20, 64, fp32_ms=0.0, fp32_launches=0, sweep_ms=6.0, sweep_launches=10,
+                          workload="none")
+    assert r["kernel"] == "sweep_kernel<64>"
+    assert abs(r["achieved"] - bench.sweep_bytes(N20, M20, 64) / 0.6e-3 / 1e9) < 1e-6
+
+
+def test_autotuner_calibrates_on_other_sources():
+    import ppr_inputs as gen
+    n = N20
+    timed = set(gen.sources(n, 64, seed=bench.replica_seed(2, 0)).tolist())
+    calib = set(bench.calibration_sources(n, 64, 0).tolist())
+    assert len(timed & calib) <= 2          # independent draws may share a node or two, not the batch
+    assert bench.calibration_sources(n, 64, 1).tolist() != bench.calibration_sources(n, 64, 0).tolist()
+
+
+def test_serving_admission_halves_then_refuses():
+    per_source = lambda k: 100 * k + 50          # workspace bytes of a batch of k
+    assert bench.admit_batch(32, 10_000, 0, per_source) == 32
+    assert bench.admit_batch(32, 250, 0, per_source) == 2
+    assert bench.admit_batch(32, 100, 0, per_source) == 0     # refused: not even one fits
+    assert bench.admit_batch(32, 0, 150, per_source) == 1     # the held workspace is reused
+    assert bench.admit_batch(3, 349, 0, per_source) == 1      # 3 does not fit, 3 // 2 does

@@ -88,20 +88,34 @@ def test_fig1_graph_approx(P):
 
 
 def test_rmat22_configuration_sampled(P):
-    """R-MAT scale 22, the approximate workload's launch (16 sources in one
-    16-column tile): counts bit-exact for a sampled source, walk budget and
-    mass checked for all."""
+    """R-MAT scale 22 with the approximate workload's 256 sources (sixteen
+    16-column tiles in one call): walk budget and mass checked for every
+    source, the no-active end state and bit-exact walk counts (oracle replay)
+    for four sources spread over the tiles, including the last one."""
     rp, ci = gen.rmat(22, 16, seed=1)
     og = O.Graph(rp, ci)
-    src = gen.sources(len(rp) - 1, 16, seed=3)
-    pi, r, counts, st = run_approx(P, rp, ci, src, k_tile=16)
+    n = og.n
+    src = gen.sources(n, 256, seed=3)
+    g = P.Graph(rp, ci)
+    k = len(src)
+    out_r = torch.empty((k, n), dtype=torch.float64, device="cuda")
+    counts = torch.empty((k, n), dtype=torch.int32, device="cuda")
+    pi, st = g.query(np.asarray(src, dtype=np.int32), P.PPR_APPROX, out_r=out_r, out_walk_counts=counts, eps=0.5,
+                     seed=SEED, k_tile=16)
+    torch.cuda.synchronize()
+    mass = pi.sum(dim=1).cpu().numpy()
+    assert np.all(np.abs(mass - 1.0) < 1e-4)
     d = np.diff(rp)
-    for i in range(len(src)):
-        assert np.all(r[i] <= d / st[i]["W"] * (1 + 1e-6))
+    for i in range(k):
         assert st[i]["walks"] <= og.m + og.n
-        assert abs(pi[i].sum() - 1.0) < 1e-4
-    oc, _, ost = O.walks(og, r[0], st[0]["W"], SEED, 0, ALPHA)
-    assert np.array_equal(counts[0], oc)
+        assert st[i]["W"] == O.speedppr_W(n, 0.5, 1.0 / n)
+    for i in (0, 77, 170, 255):
+        r = out_r[i].cpu().numpy()
+        c = counts[i].cpu().numpy().view(np.uint32)
+        assert np.all(r >= 0) and np.all(r <= d / st[i]["W"] * (1 + 1e-6))
+        oc, _, _ = O.walks(og, r, st[i]["W"], SEED, i, ALPHA)
+        assert np.array_equal(c, oc), i
+    g.close()
 
 
 def test_eps_sweep_accuracy(P):

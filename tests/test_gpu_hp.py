@@ -181,10 +181,29 @@ def rmat20():
     return rp, ci, gen.sources(len(rp) - 1, 64, seed=2)
 
 
+def check_residual_all(og, ci, src, pi, st, lam=LAM):
+    """Every returned pi_hat checked without the GPU's own bound: the oracle
+    evaluates its push residual r = (alpha e_s + (1-alpha) pi_hat P - pi_hat) /
+    alpha in FP64, and ||pi - pi_hat||_1 <= ||r||_1 (Sec. 3.2) must hold within
+    lambda up to the FP64 evaluation error."""
+    n = og.n
+    d_in_max = int(np.bincount(ci, minlength=n).max())
+    for i, s in enumerate(src):
+        x = pi[i]
+        assert x.min() >= 0
+        r = O.residual(og, int(s), x, ALPHA)
+        # node u sums d_in(u) shares plus a few rounded steps, each error at
+        # most 2^-53 of the magnitudes summed (2 sum x + alpha in all)
+        slack = (d_in_max + 5) * 2.0**-53 * (2 * x.sum() + ALPHA) / ALPHA
+        assert slack < lam / 10
+        assert np.abs(r).sum() <= min(st[i]["final_l1_residual"], lam) + slack, i
+
+
 def test_rmat20_bench_configuration(P, rmat20):
     """The benchmark's launch: 64 sources in one 64-column tile with the
     autotuned switch threshold.  Two sampled sources are checked against the
-    oracle in full; every source satisfies the certified bound and the mass
+    oracle's Algorithm 3 in full, and every source by the oracle's FP64 push
+    residual of the returned answer, besides the certified bound and the mass
     identity."""
     rp, ci, src = rmat20
     g = P.Graph(rp, ci)
@@ -197,7 +216,27 @@ def test_rmat20_bench_configuration(P, rmat20):
     for i in (0, 37):
         ref, _, _ = O.powerpush(og, int(src[i]), ALPHA, LAM)
         assert np.abs(pi[i] - ref).sum() <= 2 * LAM
-    assert np.all(pi >= 0)
+    check_residual_all(og, ci, src, pi, st)
+
+
+def test_tma_gather_pass_against_oracle(P, c0, c0_ref, rmat20):
+    """PPR_FLAG_TMA_GATHER: the FP32 passes of 64-source tiles gather the heavy
+    rows by TMA; answers within 2 lambda of the oracle (the small graph in
+    full, R-MAT scale 20 by two full solves and every source's residual)."""
+    rp, ci, src = c0
+    pi, st = run(P, rp, ci, src, k_tile=64, flags=P.PPR_FLAG_TMA_GATHER)
+    for i, s in enumerate(src):
+        assert np.abs(pi[i] - c0_ref[int(s)]).sum() <= 2 * LAM
+    check_bound_and_mass(st)
+    rp, ci, src = rmat20
+    pi, st = run(P, rp, ci, src, k_tile=64, flags=P.PPR_FLAG_TMA_GATHER)
+    check_bound_and_mass(st)
+    assert all(s["fp32_passes"] > 0 for s in st)
+    og = O.Graph(rp, ci)
+    for i in (5, 50):
+        ref, _, _ = O.powerpush(og, int(src[i]), ALPHA, LAM)
+        assert np.abs(pi[i] - ref).sum() <= 2 * LAM
+    check_residual_all(og, ci, src, pi, st)
 
 
 @pytest.mark.parametrize("k_tile", [1, 8])

@@ -106,6 +106,39 @@ def test_gradients_match_oracle(P, setup):
     m.close()
 
 
+def test_against_the_model_with_bf16_weights_only(P, setup):
+    """The model as specified keeps BF16 weights and FP32 accumulation; the
+    GPU also rounds activations to BF16 where they feed a GEMM.  Against the
+    FP64 model with only its weights rounded (W1, W2, W3, U), no activation
+    rounding: the estimate within l1 5e-3 per source (the bar of the rounded
+    comparison; activation rounding itself moves it by about 3e-5 here) and
+    every gradient block within relative l2 5e-2, about 25 BF16 unit
+    roundoffs (2^-9): four rounding points (f, h1, h2, h) and the l1
+    subgradient's sign flips near X = pi move the blocks by 1-4 %."""
+    rp, ci, g, og = setup
+    rng = np.random.default_rng(5)
+    m = P.Model(g, seed=SEED)
+    params = randomize(m, og.n, rng)
+    wonly = [Wm.bf16(p) if i in (0, 2, 4, 6) else p for i, p in enumerate(params)]
+    src = gen.sources(og.n, 5, seed=21)
+    X_gpu = m.estimate(src)
+    X_ref = Wm.warm_estimate(og, src, wonly, 128, SEED, ALPHA, rnd=None).T
+    for i in range(len(src)):
+        assert np.abs(X_gpu[i] - X_ref[i]).sum() <= 5e-3, i
+    src = gen.sources(og.n, 16, seed=23)
+    labels = np.stack([O.powerpush(og, int(s), ALPHA, 1e-10)[0] for s in src])
+    loss_gpu = m.train_step(src, labels, lr=0.0)
+    _, grads = m.get_params(grads=True)
+    S = Wm.sketches(og, src, ALPHA)
+    f = Wm.features(S, 128, SEED)
+    L, ref_grads = Wm.backward(wonly, S, f, labels.T, rnd=None)
+    assert abs(loss_gpu - L) <= 1e-3 * L
+    gparts = Wm.unflatten(grads.astype(np.float64), og.n)
+    for name, a, b in zip(["W1", "b1", "W2", "b2", "W3", "b3", "U"], gparts, ref_grads):
+        assert rel_l2(a, b) <= 5e-2, (name, rel_l2(a, b))
+    m.close()
+
+
 def test_adam_step_matches_oracle(P, setup):
     """One training step of a fresh model (Adam step 1, zero moments): the
     parameters move as the oracle's Adam step predicts from the gradients the
