@@ -128,6 +128,10 @@ typedef struct {
                                    of `sweeps` are Q1.63) */
   int32_t reserved;
   double ms_bf16;               /* HP: device time of the BF16 correction passes (part of ms_sweep) */
+  double relax;                 /* HP: over-relaxation factor w of the in-place correction passes
+                                   at the end of the call (the autotuner's choice for the graph,
+                                   else 1.15; 1 when no in-place pass ran or a stalled batch
+                                   turned it off) */
 } ppr_stats;
 
 /* Fill opts with defaults: alpha 0.2, lambda 1e-8, eps 0.5, mu 0 (=1/n),
@@ -239,11 +243,15 @@ ppr_status ppr_inject(int32_t hook, int64_t value);
  * Measure, on a calibration batch src[k], every tile width up to the smallest
  * power of two >= k (at most 64) combined with queue->sweep switch thresholds
  * of {0, 0.002, 0.02, 0.1} x m x k_tile frontier edges (Algorithm 3 fixes
- * scanThreshold = n/4 for a CPU), each timed with CUDA events on the stream.
+ * scanThreshold = n/4 for a CPU), each timed with CUDA events on the stream;
+ * then, for the fastest of these, the over-relaxation factor w of the
+ * in-place correction passes over {1.05, 1.1, 1.15, 1.2}, each judged by its
+ * mean time over three calls (their pass counts vary from call to call).
  * The fastest setting is written to *best (from *base, NULL = defaults),
  * its time to *best_ms (optional), and remembered in the graph for later HP
- * calls with k_tile = 0 / switch_edges = -1 and a k of the same power-of-two
- * bucket.  out_pi: device k x n float64 scratch for the calibration answers.
+ * calls of a k of the same power-of-two bucket: the tile width and switch
+ * for calls with k_tile = 0 / switch_edges = -1, w for every HP call (the
+ * stats report it).  out_pi: device k x n float64 scratch for the calibration answers.
  * Widths whose workspace does not fit are skipped.  Errors as ppr_sssp_query.
  */
 ppr_status ppr_autotune(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query_opts* base, double* out_pi,

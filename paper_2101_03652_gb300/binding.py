@@ -77,6 +77,7 @@ class ppr_stats(ctypes.Structure):
         ("bf16_passes", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
         ("ms_bf16", ctypes.c_double),
+        ("relax", ctypes.c_double),
     ]
 
     def as_dict(self):

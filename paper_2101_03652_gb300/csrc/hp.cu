@@ -273,12 +273,32 @@ ppr_status get_plan(ppr_graph* g, int lanes, ppr_graph::SweepPlan** out, cudaStr
   return PPR_OK;
 }
 
+// Target cost of one work item, in periods, for L lanes per row slice:
+// kItemPeriods, or less when the graph has too few items to give every
+// resident warp (the SM count x 48) about two.  A pass lasts at least as long
+// as its longest item, so on small graphs short items shorten the pass.
+static int plan_item_periods(const ppr_graph* g, int L) {
+  const int epw = 32 / L, rpw = 32 / L;
+  const int64_t total = g->m / (epw * kUnr) + g->n / rpw;  // about the periods of all rows
+  const int64_t warps = (int64_t)sm_count() * 48;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(kItemPeriods, total / (2 * warps)));
+}
+
+// Rows longer than this many in-edges are cut into pieces of it: the item
+// cost in edges, at least 256 at the full item cost (wide tiles: keep split
+// rows few) and 32 for the short items of small graphs.
+int plan_piece_edges(const ppr_graph* g, int L) {
+  const int periods = plan_item_periods(g, L);
+  return std::max(periods * (32 / L) * kUnr, periods == kItemPeriods ? 256 : 32);
+}
+
 static ppr_status build_plan(ppr_graph* g, int kt, Plan& p, cudaStream_t st) {
   const std::vector<int32_t>& d = g->h_in_deg_sorted;
   const int32_t n = (int32_t)g->n;
   const int L = kt >= 2 ? kt / 2 : 1;
   const int epw = 32 / L;                 // edges per warp step
-  const int piece = std::max(kItemPeriods * epw * kUnr, 256);  // wide tiles: keep split rows few
+  const int item_periods = plan_item_periods(g, L);
+  const int piece = plan_piece_edges(g, L);
   const int rpw = 32 / L;                 // light rows per warp
   std::vector<int4> items;
   std::vector<int32_t> npieces;
@@ -297,7 +317,7 @@ static ppr_status build_plan(ppr_graph* g, int kt, Plan& p, cudaStream_t st) {
     int cost = 0;
     while (u < n && d[u] > kLightMax) {
       int c = (d[u] + epw * kUnr - 1) / (epw * kUnr) + 1;
-      if (cost > 0 && cost + c > kItemPeriods) break;
+      if (cost > 0 && cost + c > item_periods) break;
       cost += c;
       ++u;
     }
@@ -310,7 +330,7 @@ static ppr_status build_plan(ppr_graph* g, int kt, Plan& p, cudaStream_t st) {
     int cost = 0;
     while (u < n && d[u] > 0) {
       int c = (d[u] + kUnr - 1) / kUnr + 1;  // the block's first row is its longest
-      if (cost > 0 && cost + c > kItemPeriods) break;
+      if (cost > 0 && cost + c > item_periods) break;
       cost += c;
       for (int r = 0; r < rpw && u < n && d[u] > 0; ++r) ++u;
     }
@@ -319,7 +339,7 @@ static ppr_status build_plan(ppr_graph* g, int kt, Plan& p, cudaStream_t st) {
   p.n_items_nz = (int32_t)items.size();
   while (u < n) {
     int32_t u0 = u;
-    u = (int32_t)std::min<int64_t>(n, (int64_t)u + (int64_t)kItemPeriods * rpw);
+    u = (int32_t)std::min<int64_t>(n, (int64_t)u + (int64_t)item_periods * rpw);
     items.push_back(make_int4(2, u0, u, 0));
   }
   p.n_items_all = (int32_t)items.size();
@@ -430,6 +450,7 @@ struct RefineTile {
   u64* mass = nullptr;       // [KT] device scratch for exact column sums
   bool fp32_only = false;    // no BF16 stage
   bool tma_gather = false;   // 64-source FP32 passes with TMA gathers of the heavy rows
+  float relax = 1.15f;       // over-relaxation factor of the in-place correction passes
 };
 
 constexpr float kRelax = 1.15f;  // over-relaxation of in-place correction passes
@@ -446,6 +467,7 @@ struct RefineOut {
   int passes[2] = {0, 0};    // BF16, FP32 correction passes
   float ms[2] = {0.f, 0.f};  // their device time
   int cycles = 0;
+  float relax = 1.f;         // over-relaxation in effect at the end (1 after a fallback)
 };
 
 template <int KT, typename T>
@@ -661,14 +683,15 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
     ++launches;
   }
   double rates[2] = {-1.0, -1.0};  // observed contraction per pass, BF16 / FP32
-  // In-place correction passes are over-relaxed (e <- e + w (e' - e), w = 1.15:
-  // SOR on the e-system; on R-MAT scale 20 and a Chung-Lu graph of 200,000
-  // nodes w = 1.15 measured fastest, 1.2 and above slower).  Modes with
+  // In-place correction passes are over-relaxed (e <- e + w (e' - e): SOR on
+  // the e-system).  w is the autotuner's choice for the graph, else 1.15 (on
+  // R-MAT scale 20 and a Chung-Lu graph of 200,000 nodes 1.15 measured
+  // fastest, on R-MAT scale 22 1.1; 1.2 and above slower).  Modes with
   // negative eigenvalues (near-bipartite structure) contract more slowly under
   // w > 1, so the first stalled batch turns relaxation off for the query.
   // Synchronous measured passes are never relaxed; every stop is certified by
   // an exact pass whatever w does.
-  float relax = kRelax;
+  float relax = t.relax;
   for (int cycle = 0;; ++cycle) {
     if (cycle >= 8) {
       set_error("refinement did not certify within 8 cycles");
@@ -859,7 +882,10 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
       F0 = std::max(F0, Dc * alpha);
       if (warm_x0 && cycle == 0) r0[c] = Dc;  // measured ||r(x0)||_1 of the model's estimate
     }
-    if (ok) return PPR_OK;
+    if (ok) {
+      ro.relax = relax;
+      return PPR_OK;
+    }
     if (fused) {
       prec0 = prec_next;  // the pass wrote r and z_e of the next cycle
       continue;
@@ -1077,6 +1103,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
 
     // ---- sweep phase
     int sweeps = 0, fp32_passes = 0, bf16_passes = 0, refine_cycles = 0;
+    float relax_end = 1.f;
     std::vector<double> bound(KT, 0.0);
     u64* xfinal = pi;  // the estimate to output
     // the no-active end state also needs the frontier emptied
@@ -1140,12 +1167,14 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
       rt.mass = mass;
       rt.fp32_only = (o.flags & PPR_FLAG_FP32_ONLY) != 0;
       rt.tma_gather = (o.flags & PPR_FLAG_TMA_GATHER) != 0;
+      rt.relax = g->tuned_relax[tune_bucket(k)] > 0.f ? g->tuned_relax[tune_bucket(k)] : kRelax;
       RefineOut ro;
       status = run_refine<KT>(g, plan, sweep_grid, grid_ew, sa, rt, resid, hpin, sweeps, launches, bound, r0,
                               ms_sweep, ro, es0, es1, st);
       bf16_passes = ro.passes[0];
       fp32_passes = ro.passes[1];
       refine_cycles = ro.cycles;
+      relax_end = ro.relax;
       ms_bf16 += ro.ms[0];
       ms_fp32 += ro.ms[1];
       if (status != PPR_OK) break;
@@ -1322,6 +1351,7 @@ static ppr_status run_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_
         s.fp32_passes = fp32_passes;
         s.bf16_passes = bf16_passes;
         s.refine_cycles = refine_cycles;
+        s.relax = relax_end;
       }
     }
   }
@@ -1370,7 +1400,7 @@ int hp_tile_width(const ppr_graph* g, int32_t k, int32_t k_tile) {
 size_t hp_workspace_bytes(const ppr_graph* g, int kt, int max_sweeps) {
   const size_t cells = (size_t)g->n * kt;
   const int L = kt >= 2 ? kt / 2 : 1;  // lanes per row of the Q1.63 passes
-  const int piece = std::max(kItemPeriods * (32 / L) * kUnr, 256);
+  const int piece = plan_piece_edges(g, L);
   const std::vector<int32_t>& d = g->h_in_deg_sorted;
   size_t n_split = 0;
   while (n_split < d.size() && d[n_split] > piece) ++n_split;

@@ -125,6 +125,7 @@ struct ppr_graph {
   // autotuned settings per k bucket (ceil(log2 k), 0..6); 0 / negative = untuned
   int tuned_kt[7] = {0, 0, 0, 0, 0, 0, 0};
   double tuned_switch_frac[7] = {-1, -1, -1, -1, -1, -1, -1};
+  float tuned_relax[7] = {0, 0, 0, 0, 0, 0, 0};  // over-relaxation of the in-place passes; 0 = default
   // per tile width: the sweep work list (index = log2 of the tile width, widths 1..64)
   struct SweepPlan {
     int kt = 0;

@@ -38,7 +38,7 @@ def test_default_opts_and_struct_layout():
     assert o.k_tile == 0 and o.epoch_num == 0 and o.switch_edges == -1 and o.max_sweeps == 0
     # layout fixed by include/ppr.h (x86-64 and aarch64 LP64 agree)
     assert ctypes.sizeof(binding.ppr_query_opts) == 72
-    assert ctypes.sizeof(binding.ppr_stats) == 152
+    assert ctypes.sizeof(binding.ppr_stats) == 160
 
 
 @pytest.mark.parametrize("case", ["sink", "self_loop", "unsorted", "out_of_range", "bad_rowptr"])
