@@ -245,8 +245,9 @@ ppr_status ppr_inject(int32_t hook, int64_t value);
  * of {0, 0.002, 0.02, 0.1} x m x k_tile frontier edges (Algorithm 3 fixes
  * scanThreshold = n/4 for a CPU), each timed with CUDA events on the stream;
  * then, for the fastest of these, the over-relaxation factor w of the
- * in-place correction passes over {1.05, 1.1, 1.15, 1.2}, each judged by its
- * mean time over three calls (their pass counts vary from call to call).
+ * in-place correction passes over {1.05, 1.1, 1.15}, each judged by its mean
+ * time over three calls (their pass counts vary from call to call; a factor
+ * under which a call does not certify is skipped).
  * The fastest setting is written to *best (from *base, NULL = defaults),
  * its time to *best_ms (optional), and remembered in the graph for later HP
  * calls of a k of the same power-of-two bucket: the tile width and switch

@@ -77,24 +77,31 @@ extern "C" ppr_status ppr_autotune(ppr_graph* g, const int32_t* src, int32_t k, 
   // updates is not fixed), so each candidate is judged by its mean time over
   // three calls (a factor that stalls now and then, and falls back to plain
   // passes, loses)
-  const float ws[] = {1.05f, 1.1f, 1.15f, 1.2f};
+  const float ws[] = {1.05f, 1.1f, 1.15f};
   constexpr int kReps = 3;
   float best_w = 0.f;
   double best_wt = INFINITY;
-  for (int i = 0; i < 4 && s == PPR_OK && std::isfinite(best_t); ++i) {
+  for (int i = 0; i < 3 && s == PPR_OK && std::isfinite(best_t); ++i) {
     g->tuned_relax[b] = ws[i];
     double sum = 0.0;
+    bool failed = false;
     for (int rep = 0; rep < kReps && s == PPR_OK; ++rep) {
       cudaEventRecord(e0, st);
       s = ppr_sssp_query(g, src, k, PPR_HP, &best_o, out_pi, nullptr, nullptr, nullptr, st);
       cudaEventRecord(e1, st);
+      if (s == PPR_ERR_NOT_CONVERGED) {
+        // a factor under which a call does not certify is not a candidate
+        s = PPR_OK;
+        failed = true;
+        break;
+      }
       if (s != PPR_OK) break;
       cudaEventSynchronize(e1);
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       sum += ms;
     }
-    if (s == PPR_OK && sum / kReps < best_wt) {
+    if (s == PPR_OK && !failed && sum / kReps < best_wt) {
       best_wt = sum / kReps;
       best_w = ws[i];
     }

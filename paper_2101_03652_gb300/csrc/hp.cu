@@ -273,23 +273,16 @@ ppr_status get_plan(ppr_graph* g, int lanes, ppr_graph::SweepPlan** out, cudaStr
   return PPR_OK;
 }
 
-// Target cost of one work item, in periods, for L lanes per row slice:
-// kItemPeriods, or less when the graph has too few items to give every
-// resident warp (the SM count x 48) about two.  A pass lasts at least as long
-// as its longest item, so on small graphs short items shorten the pass.
-static int plan_item_periods(const ppr_graph* g, int L) {
-  const int epw = 32 / L, rpw = 32 / L;
-  const int64_t total = g->m / (epw * kUnr) + g->n / rpw;  // about the periods of all rows
-  const int64_t warps = (int64_t)sm_count() * 48;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(kItemPeriods, total / (2 * warps)));
-}
-
 // Rows longer than this many in-edges are cut into pieces of it: the item
-// cost in edges, at least 256 at the full item cost (wide tiles: keep split
-// rows few) and 32 for the short items of small graphs.
+// cost in edges, at least 256 (wide tiles: keep split rows few).  Shorter
+// items on small graphs (down to 32 edges, so that every resident warp gets
+// about two items) shortened the FP32 pass of a 10,000-node graph from 14.8
+// to 8.4 us, but the updates, almost all concurrent, then behave like
+// synchronous ones: 69 instead of 50 passes, and with over-relaxation some
+// queries stalled until the refinement gave up.  Items keep the full cost.
 int plan_piece_edges(const ppr_graph* g, int L) {
-  const int periods = plan_item_periods(g, L);
-  return std::max(periods * (32 / L) * kUnr, periods == kItemPeriods ? 256 : 32);
+  (void)g;
+  return std::max(kItemPeriods * (32 / L) * kUnr, 256);
 }
 
 static ppr_status build_plan(ppr_graph* g, int kt, Plan& p, cudaStream_t st) {
@@ -297,7 +290,7 @@ static ppr_status build_plan(ppr_graph* g, int kt, Plan& p, cudaStream_t st) {
   const int32_t n = (int32_t)g->n;
   const int L = kt >= 2 ? kt / 2 : 1;
   const int epw = 32 / L;                 // edges per warp step
-  const int item_periods = plan_item_periods(g, L);
+  const int item_periods = kItemPeriods;
   const int piece = plan_piece_edges(g, L);
   const int rpw = 32 / L;                 // light rows per warp
   std::vector<int4> items;
