@@ -170,7 +170,13 @@ ppr_status ppr_graph_load(const int64_t* row_ptr, const int32_t* col_idx, int64_
  * (stats[i].final_l1_residual).  Flags select the other dense phases (all
  * passes Q1.63, synchronous PowItr passes, Algorithm 3's epochs).  APPROX
  * follows Algorithm 4.  Work runs on `cuda_stream`; the call returns after
- * the stream has finished the query.  Errors: PPR_ERR_ARG, PPR_ERR_ADMIT (state does not
+ * the stream has finished the query.  HP correction passes keep the most
+ * gathered rows of their tile persisting in L2 (a per-launch access-policy
+ * window): the call raises the CUDA context's persisting-L2 limit to 48 MB
+ * if it is lower, and after each batch of passes turns every persisting line
+ * of the context back to normal (cudaCtxResetPersistingL2Cache), which also
+ * affects windows other work of the same process set.  Errors: PPR_ERR_ARG,
+ * PPR_ERR_ADMIT (state does not
  * fit in free device memory), PPR_ERR_NOT_CONVERGED, PPR_ERR_OOM, PPR_ERR_CUDA.
  */
 ppr_status ppr_sssp_query(ppr_graph* g, const int32_t* src, int32_t k, ppr_mode mode,
