@@ -41,6 +41,7 @@ struct RefArgs {
   float* heavy_acc;
   unsigned int* heavy_cnt;
   double* resid;       // [KT] sums of |e_new - e_old| (NULL: not measured)
+  int light_first = 1; // in-place passes: deal the work list from its light end
 };
 
 // a lane loads 16 B of a node's tile row (V values of T); L lanes cover the row
@@ -335,7 +336,15 @@ __device__ __forceinline__ void refine_resid_block(float (&sred)[8][KT], double*
   }
 }
 
-// MEAS: the measured (synchronous) pass of a batch, which also sums |e' - e|
+// MEAS: the measured (synchronous) pass of a batch, which also sums |e' - e|.
+// An in-place pass (asynchronous updates) with a.light_first deals the work
+// list from its light end: the light rows (at most 16 in-edges, 90 % of the
+// rows of an R-MAT graph, 12 % of its edges) are updated first, and the rows
+// with many in-edges, which hold 88 % of the edges, then gather their fresh
+// values in the same pass.  Dealt from the heavy end instead, those gathers
+// read the light rows' values of the previous pass: R-MAT scale 22 took 46.7
+// instead of 38.8 passes per 64-source tile, scale 20 39.5 instead of 37.8
+// (and alternating the two directions 57.5).
 template <int KT, typename T, bool MEAS>
 __global__ void __launch_bounds__(256, (RefTune<KT, T, MEAS>::MIN_BLOCKS)) refine_pass_kernel(RefArgs a) {
   constexpr int V = RLay<KT, T>::V, L = RLay<KT, T>::L;
@@ -346,7 +355,7 @@ __global__ void __launch_bounds__(256, (RefTune<KT, T, MEAS>::MIN_BLOCKS)) refin
   for (int q = 0; q < V; ++q) res[q] = 0.f;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < a.n_items; it += nwarps)
-    refine_item<KT, T, MEAS>(a, __ldg(&a.items[it]), lane, slot, res);
+    refine_item<KT, T, MEAS>(a, __ldg(&a.items[(MEAS || !a.light_first) ? it : a.n_items - 1 - it]), lane, slot, res);
   if (!MEAS) return;
   __shared__ float sred[8][KT];
 #pragma unroll
