@@ -172,10 +172,11 @@ ppr_status ppr_graph_load(const int64_t* row_ptr, const int32_t* col_idx, int64_
  * follows Algorithm 4.  Work runs on `cuda_stream`; the call returns after
  * the stream has finished the query.  HP correction passes keep the most
  * gathered rows of their tile persisting in L2 (a per-launch access-policy
- * window): the call raises the CUDA context's persisting-L2 limit to 48 MB
- * if it is lower, and after each batch of passes turns every persisting line
- * of the context back to normal (cudaCtxResetPersistingL2Cache), which also
- * affects windows other work of the same process set.  Errors: PPR_ERR_ARG,
+ * window): for each batch of these passes the call raises the CUDA
+ * context's persisting-L2 limit to 48 MB if it is lower, and after the batch
+ * turns every persisting line of the context back to normal
+ * (cudaCtxResetPersistingL2Cache) and restores the limit, which also affects
+ * windows that other work of the same process set.  Errors: PPR_ERR_ARG,
  * PPR_ERR_ADMIT (state does not
  * fit in free device memory), PPR_ERR_NOT_CONVERGED, PPR_ERR_OOM, PPR_ERR_CUDA.
  */

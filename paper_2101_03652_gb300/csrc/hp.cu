@@ -486,36 +486,62 @@ static ppr_status refine_kernel_setup(ppr_graph* g, Plan** plan, int* grid, int*
 // unchanged): 1.46 instead of 1.54 ms per FP32 pass there (a 24 MB window
 // gave 1.49, 80 or 120 MB slower than none: the set-aside is at most about
 // 84 MB of the 126 MB L2).  The persisting set-aside is a limit of the
-// process's CUDA context; the library raises it to kPersistBytes at most
-// (never lowers it) and turns its persisting lines back to normal at the
-// end of each query.
+// process's CUDA context, and while it is raised other kernels lose that
+// part of L2 (the SpeedPPR push passes ran 40 % slower with 80 MB set
+// aside and no window of their own), so it is raised for the correction
+// batches only: set before a batch, and after the batch its persisting lines
+// are turned back to normal and the limit restored.
 constexpr size_t kPersistBytes = (size_t)48 << 20;
 
-struct HotWindow {
+class HotWindow {
+ public:
   bool on = false;
   size_t bytes = 0;
-};
 
-static HotWindow hot_window_setup() {
-  HotWindow w;
-  int dev = 0, max_persist = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess ||
-      max_persist <= 0) {
-    (void)cudaGetLastError();
-    return w;
+  HotWindow() {
+    int dev = 0, max_persist = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess ||
+        max_persist <= 0 || cudaDeviceGetLimit(&prev_, cudaLimitPersistingL2CacheSize) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return;
+    }
+    bytes = std::max(prev_, std::min(kPersistBytes, (size_t)max_persist));
+    on = true;
   }
-  size_t cur = 0;
-  cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
-  const size_t want = std::min(kPersistBytes, (size_t)max_persist);
-  if (cur < want && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) {
-    (void)cudaGetLastError();
-    return w;
+  ~HotWindow() { end(); }
+  HotWindow(const HotWindow&) = delete;
+  HotWindow& operator=(const HotWindow&) = delete;
+
+  // before a batch of correction passes: the set-aside for the window
+  cudaError_t begin() {
+    if (!on || raised_ || bytes <= prev_) return cudaSuccess;
+    const cudaError_t e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, bytes);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      on = false;  // run the passes without the window
+      return cudaSuccess;
+    }
+    raised_ = true;
+    return cudaSuccess;
   }
-  w.on = true;
-  w.bytes = std::max(cur, want);
-  return w;
-}
+  // after the batch (its stream synchronised): persisting lines back to
+  // normal, the limit back to what it was
+  cudaError_t end() {
+    if (!on) return cudaSuccess;
+    cudaError_t e = cudaCtxResetPersistingL2Cache();
+    if (raised_) {
+      const cudaError_t e2 = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, prev_);
+      if (e == cudaSuccess) e = e2;
+      raised_ = false;
+    }
+    return e;
+  }
+
+ private:
+  size_t prev_ = 0;
+  bool raised_ = false;
+};
 
 // launch a correction pass with the head of its gathered tile (base, tile
 // bytes) persisting in L2 when the window is on
@@ -709,7 +735,7 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
     }
   }
   unsigned int* h_status = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(hpin) + 64 * 8);
-  const HotWindow hot = hot_window_setup();
+  HotWindow hot;
 
   const double slack = (double)m * 0.5 / kFixOne / alpha;
   // goal of the correction passes: after the fold the exact pass measures
@@ -795,6 +821,7 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
       ra.items = fp->d_items;
       ra.npieces = fp->d_npieces;
       PPR_CUDA_TRY(cudaMemsetAsync(resid, 0, 64 * 8, st));
+      PPR_CUDA_TRY(hot.begin());
       PPR_CUDA_TRY(cudaEventRecord(es0, st));
       for (int j = 0; j < S; ++j) {
         const bool last = j == S - 1;
@@ -838,9 +865,9 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
       PPR_CUDA_TRY(cudaMemcpyAsync(hpin, resid, 64 * 8, cudaMemcpyDeviceToHost, st));
       if (use_tma) PPR_CUDA_TRY(cudaMemcpyAsync(h_status, ta.status, 4, cudaMemcpyDeviceToHost, st));
       PPR_CUDA_TRY(cudaStreamSynchronize(st));
-      // the batch is done: its persisting lines back to normal before the
-      // fold and the exact pass, which gather other arrays
-      if (hot.on) PPR_CUDA_TRY(cudaCtxResetPersistingL2Cache());
+      // the batch is done: its persisting lines back to normal and the
+      // set-aside returned before the fold and the exact pass
+      PPR_CUDA_TRY(hot.end());
       if (use_tma && *h_status) {
         set_error("a TMA row-gather wait timed out in a correction pass");
         return PPR_ERR_CUDA;
@@ -864,7 +891,13 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
         rate = std::min(1.0 - alpha, std::max(0.05, std::pow(Fm / F, 1.0 / S)));
       F = Fm;
       if (corr_pending) break;
-      if (stalled && relax != 1.f) {
+      // a stall within 100x of the precision's floor is that floor (the stage
+      // is done); a stall above it, with over-relaxation on, is a mode that
+      // w > 1 amplifies: the stage is retried without over-relaxation.
+      // (Turning relaxation off at the floor as well wasted a batch there and
+      // left the rest of the query unrelaxed.)
+      const bool near_floor = F <= 100.0 * floor_rel[prec] * F0;
+      if (stalled && relax != 1.f && !near_floor) {
         relax = 1.f;  // retry the stage without over-relaxation
         rates[0] = rates[1] = -1.0;
         continue;
