@@ -127,7 +127,9 @@ def fp32_pass_bytes_min(n: int, m: int, kt: int) -> int:
 TRAFFIC_FILES = {
     # kernel family: (committed ncu summary, sources the capture was taken on)
     "sweep_kernel": ("sweep_kernel_traffic.json", ("sweep_kernel.cuh",)),
-    "refine_pass_kernel": ("refine_pass_kernel_traffic.json", ("refine_kernel.cuh", "f32_lanes.cuh", "sweep_kernel.cuh")),
+    # the FP32 pass's launch (its L2 window, the order of its work list) is set in hp.cu
+    "refine_pass_kernel": ("refine_pass_kernel_traffic.json",
+                           ("refine_kernel.cuh", "f32_lanes.cuh", "sweep_kernel.cuh", "hp.cu")),
     "walk_kernel": ("walk_kernel_traffic.json", ("walk_kernel.cuh",)),
 }
 
@@ -150,7 +152,12 @@ def ncu_traffic(workload: str, kernel: str = "sweep_kernel"):
     try:
         with open(path) as f:
             rec = json.load(f)
-        if rec.get("kernel_source_sha") == kernel_source_sha(sources) and workload in rec.get("workloads", []):
+        if rec.get("kernel_source_sha") != kernel_source_sha(sources):
+            return None
+        per = rec.get("per_workload", {})
+        if workload in per:
+            return float(per[workload]["dram_bytes_per_launch"])
+        if workload in rec.get("workloads", []):
             return float(rec["dram_bytes_per_launch"])
     except Exception:
         pass

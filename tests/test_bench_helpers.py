@@ -45,7 +45,9 @@ def test_traffic_record_follows_the_kernel_source(monkeypatch, kernel, workload)
     with open(bench.os.path.join(bench.ROOT, "profiles", fname)) as f:
         rec = json.load(f)
     if rec["kernel_source_sha"] == bench.kernel_source_sha(sources):
-        assert bench.ncu_traffic(workload, kernel) == float(rec["dram_bytes_per_launch"])
+        per = rec.get("per_workload", {})
+        want = per[workload]["dram_bytes_per_launch"] if workload in per else rec["dram_bytes_per_launch"]
+        assert bench.ncu_traffic(workload, kernel) == float(want)
     else:
         # the kernel changed since the capture: the line reports no traffic
         assert bench.ncu_traffic(workload, kernel) is None
