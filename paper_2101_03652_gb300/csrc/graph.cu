@@ -37,7 +37,6 @@ const char* last_error_cstr() { return g_last_error.c_str(); }
 static std::atomic<int64_t> g_inject_free{-1};
 static std::atomic<int64_t> g_inject_alloc{0};
 
-int64_t injected_free_cap() { return g_inject_free.load(); }
 size_t admission_free_bytes(size_t free_bytes) {
   const int64_t cap = g_inject_free.load();
   return cap >= 0 ? std::min(free_bytes, (size_t)cap) : free_bytes;

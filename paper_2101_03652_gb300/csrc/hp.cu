@@ -280,18 +280,14 @@ ppr_status get_plan(ppr_graph* g, int lanes, ppr_graph::SweepPlan** out, cudaStr
 // to 8.4 us, but the updates, almost all concurrent, then behave like
 // synchronous ones: 69 instead of 50 passes, and with over-relaxation some
 // queries stalled until the refinement gave up.  Items keep the full cost.
-int plan_piece_edges(const ppr_graph* g, int L) {
-  (void)g;
-  return std::max(kItemPeriods * (32 / L) * kUnr, 256);
-}
+static int plan_piece_edges(int L) { return std::max(kItemPeriods * (32 / L) * kUnr, 256); }
 
 static ppr_status build_plan(ppr_graph* g, int kt, Plan& p, cudaStream_t st) {
   const std::vector<int32_t>& d = g->h_in_deg_sorted;
   const int32_t n = (int32_t)g->n;
   const int L = kt >= 2 ? kt / 2 : 1;
   const int epw = 32 / L;                 // edges per warp step
-  const int item_periods = kItemPeriods;
-  const int piece = plan_piece_edges(g, L);
+  const int piece = plan_piece_edges(L);
   const int rpw = 32 / L;                 // light rows per warp
   std::vector<int4> items;
   std::vector<int32_t> npieces;
@@ -310,7 +306,7 @@ static ppr_status build_plan(ppr_graph* g, int kt, Plan& p, cudaStream_t st) {
     int cost = 0;
     while (u < n && d[u] > kLightMax) {
       int c = (d[u] + epw * kUnr - 1) / (epw * kUnr) + 1;
-      if (cost > 0 && cost + c > item_periods) break;
+      if (cost > 0 && cost + c > kItemPeriods) break;
       cost += c;
       ++u;
     }
@@ -323,7 +319,7 @@ static ppr_status build_plan(ppr_graph* g, int kt, Plan& p, cudaStream_t st) {
     int cost = 0;
     while (u < n && d[u] > 0) {
       int c = (d[u] + kUnr - 1) / kUnr + 1;  // the block's first row is its longest
-      if (cost > 0 && cost + c > item_periods) break;
+      if (cost > 0 && cost + c > kItemPeriods) break;
       cost += c;
       for (int r = 0; r < rpw && u < n && d[u] > 0; ++r) ++u;
     }
@@ -332,7 +328,7 @@ static ppr_status build_plan(ppr_graph* g, int kt, Plan& p, cudaStream_t st) {
   p.n_items_nz = (int32_t)items.size();
   while (u < n) {
     int32_t u0 = u;
-    u = (int32_t)std::min<int64_t>(n, (int64_t)u + (int64_t)item_periods * rpw);
+    u = (int32_t)std::min<int64_t>(n, (int64_t)u + (int64_t)kItemPeriods * rpw);
     items.push_back(make_int4(2, u0, u, 0));
   }
   p.n_items_all = (int32_t)items.size();
@@ -483,9 +479,10 @@ static ppr_status refine_kernel_setup(ppr_graph* g, Plan** plan, int* grid, int*
 // traffic for 4.6 GB of algorithmic bytes.  The correction passes therefore
 // mark the first kPersistBytes of the gathered tile as persisting in L2 (an
 // access-policy window given per launch, so the caller's stream is left
-// unchanged): 1.46 instead of 1.54 ms per FP32 pass there (a 24 MB window
-// gave 1.49, 80 or 120 MB slower than none: the set-aside is at most about
-// 84 MB of the 126 MB L2).  The persisting set-aside is a limit of the
+// unchanged): 1.404 instead of 1.459 ms per FP32 pass there, 326.7 instead
+// of 334.3 us on R-MAT scale 20 (24, 32 and 64 MB windows gave less, 80 or
+// 120 MB slower than none: the set-aside is at most about 84 MB of the
+// 126 MB L2).  The persisting set-aside is a limit of the
 // process's CUDA context, and while it is raised other kernels lose that
 // part of L2 (the SpeedPPR push passes ran 40 % slower with 80 MB set
 // aside and no window of their own), so it is raised for the correction
@@ -1505,7 +1502,7 @@ int hp_tile_width(const ppr_graph* g, int32_t k, int32_t k_tile) {
 size_t hp_workspace_bytes(const ppr_graph* g, int kt, int max_sweeps) {
   const size_t cells = (size_t)g->n * kt;
   const int L = kt >= 2 ? kt / 2 : 1;  // lanes per row of the Q1.63 passes
-  const int piece = plan_piece_edges(g, L);
+  const int piece = plan_piece_edges(L);
   const std::vector<int32_t>& d = g->h_in_deg_sorted;
   size_t n_split = 0;
   while (n_split < d.size() && d[n_split] > piece) ++n_split;

@@ -66,10 +66,9 @@ struct DevBuf {
   T* as() const { return static_cast<T*>(ptr); }
 };
 
-// Host-side fault injection for the tests of the error paths (ppr_inject):
-// a cap on the free device bytes the admission checks see (< 0: off), and a
-// countdown after which a workspace allocation fails as out of memory (<= 0: off).
-int64_t injected_free_cap();
+// Free device bytes as the admission checks see them: the measured value,
+// capped by the host-side test hook of ppr_inject (PPR_INJECT_FREE_BYTES).
+// The other hook (PPR_INJECT_ALLOC_FAIL) acts in DevBuf::ensure.
 size_t admission_free_bytes(size_t free_bytes);
 
 struct Workspace {
