@@ -566,6 +566,31 @@ static cudaError_t launch_refine_pass(int grid, const RefArgs& ra, const HotWind
   return cudaLaunchKernelEx(&cfg, refine_pass_kernel<KT, T, MEAS>, ra);
 }
 
+// the exact synchronous Q1.63 pass of a refinement cycle, with the head of
+// its gathered tile z(X) persisting in L2 like the correction passes
+template <int KT>
+static cudaError_t launch_exact_pass(int grid, const SweepArgs& sa, const HotWindow& w, size_t tile_bytes,
+                                     cudaStream_t st) {
+  if (!w.on) {
+    sweep_kernel<KT, false><<<grid, 256, 0, st>>>(sa);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+  attr[0].val.accessPolicyWindow.base_ptr = const_cast<u64*>(sa.z_in);
+  attr[0].val.accessPolicyWindow.num_bytes = std::min(w.bytes, tile_bytes);
+  attr[0].val.accessPolicyWindow.hitRatio = 1.f;
+  attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+  attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, sweep_kernel<KT, false>, sa);
+}
+
 // ------------------------------------------------------------ TMA passes
 constexpr int kTmaWarps = 2;  // TMA warps per block of the 64-source FP32 pass (the rest take light rows)
 
@@ -950,14 +975,15 @@ static ppr_status run_refine(ppr_graph* g, const Plan& plan, int sweep_grid, int
       sa.ze_bf16 = prec_next == 0;
       sa.n_items = plan.n_items_all;
       sa.resid = resid;
+      PPR_CUDA_TRY(hot.begin());
       PPR_CUDA_TRY(cudaEventRecord(es0, st));
-      sweep_kernel<KT, false><<<sweep_grid, 256, 0, st>>>(sa);
+      PPR_CUDA_TRY(launch_exact_pass<KT>(sweep_grid, sa, hot, cells * 8, st));
       PPR_CUDA_TRY(cudaEventRecord(es1, st));
-      PPR_CUDA_TRY(cudaGetLastError());
       ++sweeps;
       ++launches;
       PPR_CUDA_TRY(cudaMemcpyAsync(hpin, resid, 64 * 8, cudaMemcpyDeviceToHost, st));
       PPR_CUDA_TRY(cudaStreamSynchronize(st));
+      PPR_CUDA_TRY(hot.end());
       float a_ms = 0.f;
       cudaEventElapsedTime(&a_ms, es0, es1);
       ms_sweep += a_ms;
