@@ -201,10 +201,12 @@ def make_inputs(workload: str, rank: int):
 
 
 def calibration_sources(n: int, k: int, rank: int):
-    """The autotuner's calibration batch: k sources drawn with their own seed,
-    so that the setting is chosen on other sources than the ones timed."""
+    """The autotuner's calibration batch, drawn with its own seed so that the
+    setting is chosen on other sources than the ones timed: k sources, or two
+    batches' worth (2k) when k >= 64, where the tuner's k bucket is the same
+    and two tiles per call average the batch-to-batch spread of pass counts."""
     import ppr_inputs as gen
-    return gen.sources(n, k, seed=replica_seed(CALIB_SEED, rank))
+    return gen.sources(n, 2 * k if k >= 64 else k, seed=replica_seed(CALIB_SEED, rank))
 
 
 def hp_roofline(n: int, m: int, kt: int, fp32_ms: float, fp32_launches: int, sweep_ms: float, sweep_launches: int,

@@ -250,8 +250,9 @@ ppr_status ppr_inject(int32_t hook, int64_t value);
  * Measure, on a calibration batch src[k], every tile width up to the smallest
  * power of two >= k (at most 64) combined with queue->sweep switch thresholds
  * of {0, 0.002, 0.02, 0.1} x m x k_tile frontier edges (Algorithm 3 fixes
- * scanThreshold = n/4 for a CPU), each timed with CUDA events on the stream;
- * then, for the fastest of these, the over-relaxation factor w of the
+ * scanThreshold = n/4 for a CPU), each timed with CUDA events on the stream,
+ * and the three fastest again over three calls (best mean); then, for the
+ * chosen one, the over-relaxation factor w of the
  * in-place correction passes over {1.05, 1.1, 1.15}, each judged by its mean
  * time over three calls (their pass counts vary from call to call; a factor
  * under which a call does not certify is skipped).

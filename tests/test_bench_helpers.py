@@ -80,8 +80,10 @@ def test_autotuner_calibrates_on_other_sources():
     import ppr_inputs as gen
     n = N20
     timed = set(gen.sources(n, 64, seed=bench.replica_seed(2, 0)).tolist())
-    calib = set(bench.calibration_sources(n, 64, 0).tolist())
-    assert len(timed & calib) <= 2          # independent draws may share a node or two, not the batch
+    calib = bench.calibration_sources(n, 64, 0)
+    assert len(calib) == 128                # two tiles per calibration call at 64 sources
+    assert len(bench.calibration_sources(n, 10, 0)) == 10   # below 64, the same bucket needs the same k
+    assert len(timed & set(calib.tolist())) <= 4      # independent draws may share a few nodes, not the batch
     assert bench.calibration_sources(n, 64, 1).tolist() != bench.calibration_sources(n, 64, 0).tolist()
 
 
