@@ -114,6 +114,7 @@ SIGNATURES = {
     "ppr_query_state_bytes": (ctypes.c_int64, [_P, ctypes.c_int32, ctypes.c_int32]),
     "ppr_workspace_bytes": (ctypes.c_int64, [_P]),
     "ppr_inject": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64]),
+    "ppr_selftest_fixconv": (ctypes.c_int, [ctypes.c_int64, ctypes.c_uint64, _P, _P]),
     "ppr_index_build": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double, _P]),
     "ppr_index_get": (ctypes.c_int, [_P, _P]),
     "ppr_autotune": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(ppr_query_opts), _P,
@@ -262,6 +263,14 @@ def ppr_inject(hook: int, value: int):
     caps the free device bytes admission sees (value < 0: off);
     PPR_INJECT_ALLOC_FAIL makes the value-th workspace allocation fail (0: off)."""
     _check(load_library().ppr_inject(hook, value))
+
+
+def ppr_selftest_fixconv(count: int = 1 << 24, seed: int = 0x5EED, stream=None) -> list:
+    """Mismatch counts of the device's fixed-point <-> FP32/FP64 conversions
+    against CUDA's intrinsics (see include/ppr.h); all zero when they agree."""
+    out = np.zeros(5, dtype=np.int64)
+    _check(load_library().ppr_selftest_fixconv(count, seed, out.ctypes.data, _stream(stream)))
+    return out.tolist()
 
 
 def ppr_free(graph: int):

@@ -341,6 +341,15 @@ ppr_status ppr_inject(int32_t hook, int64_t value) {
 
 int64_t ppr_workspace_bytes(const ppr_graph* g) { return g ? (int64_t)g->ws.device_bytes() : -1; }
 
+ppr_status ppr_selftest_fixconv(int64_t count, uint64_t seed, int64_t* out_mismatches, void* cuda_stream) {
+  clear_error();
+  if (count < 0 || !out_mismatches) {
+    set_error("conversion self-test needs count >= 0 and out_mismatches");
+    return PPR_ERR_ARG;
+  }
+  return fixconv_selftest(count, seed, out_mismatches, (cudaStream_t)cuda_stream);
+}
+
 int64_t ppr_graph_n(const ppr_graph* g) { return g ? g->n : 0; }
 int64_t ppr_graph_m(const ppr_graph* g) { return g ? g->m : 0; }
 

@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256) output_kernel(int64_t n, const int32_t* _
     __syncthreads();
     for (int i = threadIdx.x; i < NB * KT; i += blockDim.x) {
       const int j = i / KT, c = i % KT;
-      if (j < cnt) tile[c][j] = (double)__ldg(&x[rows[j] * KT + c]) * (1.0 / kFixOne);
+      if (j < cnt) tile[c][j] = u64_to_f64<-63>(__ldg(&x[rows[j] * KT + c]));
     }
     __syncthreads();
     for (int i = threadIdx.x; i < ncols * NB; i += blockDim.x) {
@@ -1579,6 +1579,71 @@ ppr_status query_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query
     case 64: return run_hp<64>(g, src, k, o, out_pi, out_r, stats, st);
     default: set_error("k_tile must be 0, 1, 2, 4, 8, 16, 32 or 64"); return PPR_ERR_ARG;
   }
+}
+
+// ------------------------------------------- self-test of the conversions
+// The integer-only conversions of sweep_kernel.cuh against CUDA's own
+// conversion intrinsics, on counter-generated inputs: every leading-zero
+// count, exact ties of the FP32 and FP64 roundings, both signs.
+__device__ __forceinline__ u64 splitmix64(u64 x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+__global__ void fixconv_selftest_kernel(int64_t count, u64 seed, unsigned long long* bad) {
+  unsigned long long nb[5] = {0, 0, 0, 0, 0};
+  const float s63 = 1.0f / 9223372036854775808.0f;  // 2^-63, exact
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const u64 h = splitmix64(seed ^ (u64)i), h2 = splitmix64(h);
+    u64 u;
+    switch (i % 3) {
+      case 0: u = h >> (i % 64); break;
+      case 1: {  // a tie of the FP32 rounding
+        const int k = 1 + (int)(h2 % 39);
+        u = (((h | 0x800000ull) & 0xFFFFFFull) << k) | (1ull << (k - 1));
+        break;
+      }
+      default: {  // a tie of the FP64 rounding
+        const int k = 1 + (int)(h2 % 11);
+        u = (((h | (1ull << 52)) & ((1ull << 53) - 1ull)) << k) | (1ull << (k - 1));
+      }
+    }
+    if (i == 0) u = 0;
+    if (i == 3) u = ~0ull;
+    nb[0] += __float_as_uint(u64_to_f32<-63>(u)) != __float_as_uint(__ull2float_rn(u) * s63);
+    nb[1] += __float_as_uint(u64_to_f32<0>(u)) != __float_as_uint(__ull2float_rn(u));
+    nb[2] += __double_as_longlong(u64_to_f64<-63>(u)) != __double_as_longlong(__ull2double_rn(u) * (1.0 / kFixOne));
+    const long long d = (long long)h2 >> (i % 64);
+    nb[3] += __float_as_uint(sfix_to_f32(d)) != __float_as_uint(__ll2float_rn(d) * s63);
+    // |e| < 1: exponent field 0..126, either sign
+    const uint32_t eb = (uint32_t)(h2 >> 32);
+    const float e = __uint_as_float((eb & 0x807FFFFFu) | ((uint32_t)((eb >> 8) % 127u) << 23));
+    nb[4] += f32_to_sfix(e) != llrint((double)e * kFixOne);
+  }
+  for (int q = 0; q < 5; ++q)
+    if (nb[q]) atomicAdd(&bad[q], nb[q]);
+}
+
+ppr_status fixconv_selftest(int64_t count, uint64_t seed, int64_t* out_mismatches, cudaStream_t st) {
+  unsigned long long* d = nullptr;
+  PPR_CUDA_TRY(cudaMalloc((void**)&d, 5 * sizeof(unsigned long long)));
+  cudaError_t e = cudaMemsetAsync(d, 0, 5 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess && count > 0) {
+    fixconv_selftest_kernel<<<sm_count() * 8, 256, 0, st>>>(count, seed, d);
+    e = cudaGetLastError();
+  }
+  unsigned long long h[5] = {0, 0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    set_error("conversion self-test: %s", cudaGetErrorString(e));
+    return PPR_ERR_CUDA;
+  }
+  for (int q = 0; q < 5; ++q) out_mismatches[q] = (int64_t)h[q];
+  return PPR_OK;
 }
 
 }  // namespace ppr

@@ -154,6 +154,7 @@ ppr_status query_hp(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query
                     double* out_r, ppr_stats* stats, cudaStream_t st);
 ppr_status query_approx(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query_opts& o, double* out_pi,
                         double* out_r, uint32_t* out_counts, ppr_stats* stats, cudaStream_t st);
+ppr_status fixconv_selftest(int64_t count, uint64_t seed, int64_t* out_mismatches, cudaStream_t st);
 bool is_device_pointer(const void* p);
 void* device_view(void* p);
 ppr_status get_plan(ppr_graph* g, int lanes, ppr_graph::SweepPlan** out, cudaStream_t st);

@@ -356,17 +356,18 @@ __global__ void __launch_bounds__(256, (RefTune<KT, T, MEAS>::MIN_BLOCKS)) refin
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < a.n_items; it += nwarps)
     refine_item<KT, T, MEAS>(a, __ldg(&a.items[(MEAS || !a.light_first) ? it : a.n_items - 1 - it]), lane, slot, res);
-  if (!MEAS) return;
-  __shared__ float sred[8][KT];
+  if constexpr (MEAS) {
+    __shared__ float sred[8][KT];
 #pragma unroll
-  for (int off = L; off < 32; off <<= 1)
+    for (int off = L; off < 32; off <<= 1)
 #pragma unroll
-    for (int q = 0; q < V; ++q) res[q] += __shfl_xor_sync(kFull, res[q], off);
-  const int warp = threadIdx.x >> 5;
-  if (lane < L)
+      for (int q = 0; q < V; ++q) res[q] += __shfl_xor_sync(kFull, res[q], off);
+    const int warp = threadIdx.x >> 5;
+    if (lane < L)
 #pragma unroll
-    for (int q = 0; q < V; ++q) sred[warp][lane * V + q] = res[q];
-  refine_resid_block<KT>(sred, a.resid);
+      for (int q = 0; q < V; ++q) sred[warp][lane * V + q] = res[q];
+    refine_resid_block<KT>(sred, a.resid);
+  }
 }
 
 // z_e of the BF16 passes into FP32 (exact) for the FP32 passes that follow
@@ -381,16 +382,66 @@ __device__ __forceinline__ void st_one(T* p, float v) {
   else *p = __float2bfloat16_rn(v);
 }
 
-// r of a push state: rf = alpha r_push (FP32), first correction e1 = rf
+// The setup and fold kernels below stream n x KT cells.  With KT >= 4 a
+// thread takes 4 cells of one node per step, as 16-byte loads and stores:
+// one 8-byte load per thread and step kept too few bytes in flight to cover
+// the DRAM latency (the setup ran at 0.41 of the copy bandwidth).
+template <int KT>
+struct Ew {
+  static constexpr int G = KT >= 4 ? 4 : 1;  // cells per thread and step
+};
+
+__device__ __forceinline__ void ld4(const u64* p, u64 (&v)[4]) {
+  const ulonglong2 a = reinterpret_cast<const ulonglong2*>(p)[0];
+  const ulonglong2 b = reinterpret_cast<const ulonglong2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+__device__ __forceinline__ void st4(u64* p, const u64 (&v)[4]) {
+  reinterpret_cast<ulonglong2*>(p)[0] = make_ulonglong2(v[0], v[1]);
+  reinterpret_cast<ulonglong2*>(p)[1] = make_ulonglong2(v[2], v[3]);
+}
+
+__device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+__device__ __forceinline__ void st4(bf16* p, const float (&v)[4]) {
+  __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]), hi = __floats2bfloat162_rn(v[2], v[3]);
+  uint2 w;
+  w.x = *reinterpret_cast<unsigned int*>(&lo);
+  w.y = *reinterpret_cast<unsigned int*>(&hi);
+  *reinterpret_cast<uint2*>(p) = w;
+}
+
+// r of a push state: rf = alpha r_push (FP32, the fixed-point r_push rounded
+// to FP32, then times alpha), first correction e1 = rf
 template <int KT, typename T>
 __global__ void refine_setup_push_kernel(int64_t n, const u64* __restrict__ r_push, double alpha,
                                          const int32_t* __restrict__ deg, float one_minus_alpha, float* __restrict__ rf,
                                          T* __restrict__ ze) {
-  const int64_t total = n * KT;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const float v = (float)((double)r_push[i] * (alpha / kFixOne));
-    rf[i] = v;
-    st_one<T>(ze + i, v * (one_minus_alpha / (float)deg[i / KT]));
+  constexpr int G = Ew<KT>::G;
+  const int64_t groups = n * KT / G;
+  const float af = (float)alpha;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = g * G;
+    const float s = one_minus_alpha / (float)deg[i / KT];
+    if constexpr (G == 4) {
+      u64 r[4];
+      ld4(r_push + i, r);
+      float v[4], z[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        v[q] = u64_to_f32<-63>(r[q]) * af;
+        z[q] = v[q] * s;
+      }
+      st4(rf + i, v);
+      st4(ze + i, z);
+    } else {
+      const float v = u64_to_f32<-63>(r_push[i]) * af;
+      rf[i] = v;
+      st_one<T>(ze + i, v * s);
+    }
   }
 }
 
@@ -399,12 +450,32 @@ template <int KT, typename T>
 __global__ void refine_setup_resid_kernel(int64_t n, const u64* __restrict__ x_new, const u64* __restrict__ x,
                                           const int32_t* __restrict__ deg, float one_minus_alpha,
                                           float* __restrict__ rf, T* __restrict__ ze) {
-  const int64_t total = n * KT;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const long long dlt = (long long)(x_new[i] - x[i]);
-    const float v = (float)((double)dlt * (1.0 / kFixOne));
-    rf[i] = v;
-    st_one<T>(ze + i, v * (one_minus_alpha / (float)deg[i / KT]));
+  constexpr int G = Ew<KT>::G;
+  const int64_t groups = n * KT / G;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = g * G;
+    const float s = one_minus_alpha / (float)deg[i / KT];
+    u64 a[G], b[G];
+    if constexpr (G == 4) {
+      ld4(x_new + i, a);
+      ld4(x + i, b);
+    } else {
+      a[0] = x_new[i];
+      b[0] = x[i];
+    }
+    float v[G], z[G];
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+      v[q] = sfix_to_f32((long long)(a[q] - b[q]));
+      z[q] = v[q] * s;
+    }
+    if constexpr (G == 4) {
+      st4(rf + i, v);
+      st4(ze + i, z);
+    } else {
+      rf[i] = v[0];
+      st_one<T>(ze + i, z[0]);
+    }
   }
 }
 
@@ -412,13 +483,34 @@ __global__ void refine_setup_resid_kernel(int64_t n, const u64* __restrict__ x_n
 template <int KT>
 __global__ void refine_fold_kernel(int64_t n, const float* __restrict__ e, u64* __restrict__ x,
                                    const uint64_t* __restrict__ omega, u64* __restrict__ z) {
-  const int64_t total = n * KT;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const long long dlt = llrint((double)e[i] * kFixOne);
-    const long long xv = (long long)x[i] + dlt;
-    const u64 xn = xv > 0 ? (u64)xv : 0ull;
-    x[i] = xn;
-    z[i] = mulhi_round(xn, omega[i / KT]);
+  constexpr int G = Ew<KT>::G;
+  const int64_t groups = n * KT / G;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = g * G;
+    const uint64_t om = omega[i / KT];
+    float ev[G];
+    u64 xv[G], zv[G];
+    if constexpr (G == 4) {
+      const float4 e4 = reinterpret_cast<const float4*>(e + i)[0];
+      ev[0] = e4.x; ev[1] = e4.y; ev[2] = e4.z; ev[3] = e4.w;
+      ld4(x + i, xv);
+    } else {
+      ev[0] = e[i];
+      xv[0] = x[i];
+    }
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+      const long long s = (long long)xv[q] + f32_to_sfix(ev[q]);
+      xv[q] = s > 0 ? (u64)s : 0ull;
+      zv[q] = mulhi_round(xv[q], om);
+    }
+    if constexpr (G == 4) {
+      st4(x + i, xv);
+      st4(z + i, zv);
+    } else {
+      x[i] = xv[0];
+      z[i] = zv[0];
+    }
   }
 }
 

@@ -19,6 +19,70 @@ __device__ __forceinline__ u64 mulhi_round(u64 x, u64 w) {
   return hi + (lo >> 63);
 }
 
+// ------------------------------------------------- Q1.63 <-> IEEE conversions
+// Conversions between the fixed-point values and FP32/FP64 with integer
+// instructions only.  GB300 executes FP64 arithmetic, including conversions
+// from and to 64-bit integers, at a small fraction of its FP32 rate: a
+// streaming kernel doing three such operations per cell (e.g. rf = (float)
+// ((double)r * alpha / 2^63)) was bound by them, at about 0.4 of the copy
+// bandwidth.  All round to nearest, ties to even, like cvt.rn.
+
+// the float nearest to u * 2^E2 (u != 0 must land in the normal range)
+template <int E2>
+__device__ __forceinline__ float u64_to_f32(u64 u) {
+  if (u == 0) return 0.f;
+  const int lz = __clzll(u);
+  const u64 m = u << lz;                        // leading one at bit 63
+  uint32_t top = (uint32_t)(m >> 40);           // 24 significant bits
+  const u64 rest = m & 0xFFFFFFFFFFull, half = 0x8000000000ull;
+  top += (rest > half || (rest == half && (top & 1u))) ? 1u : 0u;
+  // top's leading bit adds one to the exponent field; a carry out of the
+  // 24 bits adds one more and leaves the fraction zero
+  return __uint_as_float(((uint32_t)(63 - lz + E2 + 126) << 23) + top);
+}
+
+// the double nearest to u * 2^E2
+template <int E2>
+__device__ __forceinline__ double u64_to_f64(u64 u) {
+  if (u == 0) return 0.0;
+  const int lz = __clzll(u);
+  const u64 m = u << lz;
+  u64 top = m >> 11;                            // 53 significant bits
+  const u64 rest = m & 0x7FFull, half = 0x400ull;
+  top += (rest > half || (rest == half && (top & 1ull))) ? 1ull : 0ull;
+  return __longlong_as_double((long long)(((u64)(63 - lz + E2 + 1022) << 52) + top));
+}
+
+// the float nearest to d * 2^-63 (a signed Q1.63 difference)
+__device__ __forceinline__ float sfix_to_f32(long long d) {
+  const float f = u64_to_f32<-63>(d < 0 ? 0ull - (u64)d : (u64)d);
+  return d < 0 ? -f : f;
+}
+
+// the integer nearest to e * 2^63 (e in Q1.63 units), for |e| < 1; larger
+// magnitudes, infinities and NaN give +-(2^63 - 1)
+__device__ __forceinline__ long long f32_to_sfix(float e) {
+  const uint32_t b = __float_as_uint(e);
+  const int ex = (int)((b >> 23) & 0xFFu);
+  if (ex == 0) return 0;                        // zero or subnormal: below 2^-63
+  const u64 m = (u64)((b & 0x7FFFFFu) | 0x800000u);
+  const int sh = ex - 87;                       // |e| 2^63 = m 2^(ex - 150 + 63)
+  u64 q;
+  if (sh >= 40) {
+    q = 0x7FFFFFFFFFFFFFFFull;
+  } else if (sh >= 0) {
+    q = m << sh;
+  } else if (sh < -25) {
+    q = 0;
+  } else {
+    const int k = -sh;
+    q = m >> k;
+    const u64 r = m & ((1ull << k) - 1ull), half = 1ull << (k - 1);
+    q += (r > half || (r == half && (q & 1ull))) ? 1ull : 0ull;
+  }
+  return (b >> 31) ? -(long long)q : (long long)q;
+}
+
 // ------------------------------------------------------------ sweep phase
 struct SweepArgs {
   int32_t n_items;   // work items of this pass (items over rows without in-edges come last and
@@ -96,8 +160,8 @@ __device__ __forceinline__ void row_epilogue(const SweepArgs& a, int u, int slot
     for (int q = 0; q < V; ++q) {
       const u64 xn = acc[q] + (u == a.src[slot * V + q] ? a.alpha_raw : 0ull);
       const long long d = (long long)(xn - xo[q]);
-      res[q] += (float)(d < 0 ? -d : d);
-      const float rv = (float)((double)d * (1.0 / kFixOne));
+      res[q] += u64_to_f32<0>(d < 0 ? 0ull - (u64)d : (u64)d);
+      const float rv = sfix_to_f32(d);
       a.rf_next[base + q] = rv;
       if (a.ze_bf16)
         static_cast<__nv_bfloat16*>(a.ze_next)[base + q] = __float2bfloat16_rn(rv * share);
@@ -118,7 +182,7 @@ __device__ __forceinline__ void row_epilogue(const SweepArgs& a, int u, int slot
     u64 zo[V];
     ld_vec<V, COH>(a.z_in + (size_t)u * KT + slot * V, zo);
 #pragma unroll
-    for (int q = 0; q < V; ++q) res[q] += (float)(zn[q] > zo[q] ? zn[q] - zo[q] : zo[q] - zn[q]) * iw;
+    for (int q = 0; q < V; ++q) res[q] += u64_to_f32<0>(zn[q] > zo[q] ? zn[q] - zo[q] : zo[q] - zn[q]) * iw;
   }
   if (a.z_out) st_vec<V>(a.z_out + (size_t)u * KT + slot * V, zn);
   if (a.x_out) st_vec<V>(a.x_out + (size_t)u * KT + slot * V, xn);
