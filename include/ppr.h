@@ -250,9 +250,11 @@ ppr_status ppr_inject(int32_t hook, int64_t value);
  * values (the exact reserve and residue of Sec. 4, Eq. 7) and FP32/FP64, which
  * the kernels do with integer instructions: `count` counter-generated inputs
  * (seed), each checked bit for bit against CUDA's conversion intrinsics.
- * out_mismatches (host, 5 entries) receives the mismatch counts of: Q1.63 ->
+ * out_mismatches (host, 7 entries) receives the mismatch counts of: Q1.63 ->
  * FP32, 64-bit integer -> FP32, Q1.63 -> FP64, signed Q1.63 -> FP32, FP32 ->
- * signed Q1.63 (round to nearest even, |value| < 1).  Synchronises the stream.
+ * signed Q1.63 (these round to nearest even; |value| < 1), FP32 -> Q1.63 by
+ * truncation (0 <= value < 2), and floor(integer x FP32 value) (value in
+ * [0, 1]).  Synchronises the stream.
  * Errors: PPR_ERR_ARG (count < 0, NULL out_mismatches), PPR_ERR_CUDA. */
 ppr_status ppr_selftest_fixconv(int64_t count, uint64_t seed, int64_t* out_mismatches, void* cuda_stream);
 

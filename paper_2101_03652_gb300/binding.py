@@ -268,7 +268,7 @@ def ppr_inject(hook: int, value: int):
 def ppr_selftest_fixconv(count: int = 1 << 24, seed: int = 0x5EED, stream=None) -> list:
     """Mismatch counts of the device's fixed-point <-> FP32/FP64 conversions
     against CUDA's intrinsics (see include/ppr.h); all zero when they agree."""
-    out = np.zeros(5, dtype=np.int64)
+    out = np.zeros(7, dtype=np.int64)
     _check(load_library().ppr_selftest_fixconv(count, seed, out.ctypes.data, _stream(stream)))
     return out.tolist()
 

@@ -1592,8 +1592,10 @@ __device__ __forceinline__ u64 splitmix64(u64 x) {
   return x ^ (x >> 31);
 }
 
+constexpr int kFixconvChecks = 7;
+
 __global__ void fixconv_selftest_kernel(int64_t count, u64 seed, unsigned long long* bad) {
-  unsigned long long nb[5] = {0, 0, 0, 0, 0};
+  unsigned long long nb[kFixconvChecks] = {};
   const float s63 = 1.0f / 9223372036854775808.0f;  // 2^-63, exact
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
     const u64 h = splitmix64(seed ^ (u64)i), h2 = splitmix64(h);
@@ -1621,20 +1623,27 @@ __global__ void fixconv_selftest_kernel(int64_t count, u64 seed, unsigned long l
     const uint32_t eb = (uint32_t)(h2 >> 32);
     const float e = __uint_as_float((eb & 0x807FFFFFu) | ((uint32_t)((eb >> 8) % 127u) << 23));
     nb[4] += f32_to_sfix(e) != llrint((double)e * kFixOne);
+    // truncation of x 2^63 for 0 <= x < 2, and floor(mu x) with mu x exact in
+    // FP64 (mu a 29-bit integer times a power of two), 0 <= x <= 1
+    const float x2 = __uint_as_float(((uint32_t)(h >> 32) & 0x7FFFFFu) | ((uint32_t)((h >> 13) % 128u) << 23));
+    nb[5] += f32_to_ufix_trunc(x2) != __double2ull_rz((double)x2 * kFixOne);
+    const float x1 = fminf(x2 * 0.5f, 1.0f);
+    const u64 mu = (h2 & ((1ull << 29) - 1ull)) << (int)((h >> 40) % 35u);
+    nb[6] += mul_fix_f32(mu, x1) != __double2ull_rz((double)mu * (double)x1);
   }
-  for (int q = 0; q < 5; ++q)
+  for (int q = 0; q < kFixconvChecks; ++q)
     if (nb[q]) atomicAdd(&bad[q], nb[q]);
 }
 
 ppr_status fixconv_selftest(int64_t count, uint64_t seed, int64_t* out_mismatches, cudaStream_t st) {
   unsigned long long* d = nullptr;
-  PPR_CUDA_TRY(cudaMalloc((void**)&d, 5 * sizeof(unsigned long long)));
-  cudaError_t e = cudaMemsetAsync(d, 0, 5 * sizeof(unsigned long long), st);
+  PPR_CUDA_TRY(cudaMalloc((void**)&d, kFixconvChecks * sizeof(unsigned long long)));
+  cudaError_t e = cudaMemsetAsync(d, 0, kFixconvChecks * sizeof(unsigned long long), st);
   if (e == cudaSuccess && count > 0) {
     fixconv_selftest_kernel<<<sm_count() * 8, 256, 0, st>>>(count, seed, d);
     e = cudaGetLastError();
   }
-  unsigned long long h[5] = {0, 0, 0, 0, 0};
+  unsigned long long h[kFixconvChecks] = {};
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(d);
@@ -1642,7 +1651,7 @@ ppr_status fixconv_selftest(int64_t count, uint64_t seed, int64_t* out_mismatche
     set_error("conversion self-test: %s", cudaGetErrorString(e));
     return PPR_ERR_CUDA;
   }
-  for (int q = 0; q < 5; ++q) out_mismatches[q] = (int64_t)h[q];
+  for (int q = 0; q < kFixconvChecks; ++q) out_mismatches[q] = (int64_t)h[q];
   return PPR_OK;
 }
 

@@ -26,6 +26,7 @@
 #include <random>
 #include <vector>
 
+#include "fixconv.cuh"
 #include "ppr_internal.cuh"
 
 namespace ppr {
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(256) basis_kernel(BasisArgs a) {
           const float sg = a.sig[c];
           const float X = sg > 0.f ? y / sg : s;
           if constexpr (PASS == 4) {
-            const u64 xf = (u64)((double)X * kFixOne);
+            const u64 xf = f32_to_ufix_trunc(X);
             const u64 om = a.omega[u];
             const u64 hi = __umul64hi(xf, om), lo = xf * om;
             if (c < a.kt) {
@@ -343,7 +344,7 @@ __global__ void __launch_bounds__(256) basis_kernel(BasisArgs a) {
             // the estimate already holds all the mass); z = x (1-alpha)/d
             if (c < a.kt) {
               const long long mu = (long long)(kFixOneRaw - a.mass[c]);
-              const u64 add = mu > 0 ? (u64)((double)mu * (double)X) : 0ull;
+              const u64 add = mu > 0 ? mul_fix_f32((u64)mu, X) : 0ull;
               const u64 xn = a.xin[(size_t)u * a.kt + c] + add;
               const u64 om = a.omega[u];
               const u64 hi = __umul64hi(xn, om), lo = xn * om;

@@ -235,7 +235,7 @@ def test_injection_hooks_and_workspace_query_without_device():
 
 def test_conversion_selftest_rejects_bad_arguments_without_device():
     lib = P.load_library()
-    out = np.zeros(5, dtype=np.int64)
+    out = np.zeros(7, dtype=np.int64)
     assert lib.ppr_selftest_fixconv(-1, 0, out.ctypes.data, None) == binding.PPR_ERR_ARG
     assert lib.ppr_selftest_fixconv(16, 0, None, None) == binding.PPR_ERR_ARG
     assert b"conversion self-test" in lib.ppr_last_error()
