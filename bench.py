@@ -129,7 +129,7 @@ TRAFFIC_FILES = {
     "sweep_kernel": ("sweep_kernel_traffic.json", ("sweep_kernel.cuh",)),
     # the FP32 pass's launch (its L2 window, the order of its work list) is set in hp.cu
     "refine_pass_kernel": ("refine_pass_kernel_traffic.json",
-                           ("refine_kernel.cuh", "f32_lanes.cuh", "sweep_kernel.cuh", "hp.cu")),
+                           ("refine_kernel.cuh", "f32_lanes.cuh", "sweep_kernel.cuh", "fixconv.cuh", "hp.cu")),
     "walk_kernel": ("walk_kernel_traffic.json", ("walk_kernel.cuh",)),
 }
 
