@@ -280,6 +280,83 @@ def hp_side_record(P, label: str, rp, ci, src, steps: int, warmup: int, rank: in
             "clocks": clk.summary()}
 
 
+def approx_roofline(st, steps: int, n_tiles: int, walk_ms: float, kt: int, indexed: bool, workload: str):
+    """Roofline entry of a SpeedPPR step's dominant kernel: the walks (two 32 B
+    sectors per move and per endpoint) or, with the index, the index reads
+    (per walk one 4 B entry and the two 32 B sectors of its endpoint's count
+    and estimate); st are the stats of the last step, walk_ms the kernel's
+    event time summed over the timed steps."""
+    walks = sum(x["walks"] for x in st)
+    if indexed:
+        per_launch = 68 * walks / n_tiles
+        kernel_name = f"index_query_kernel<{kt}>"
+    else:
+        per_launch = 64 * (sum(x["walk_steps"] for x in st) + walks) / n_tiles
+        kernel_name = f"walk_kernel<{kt}>"
+    avg_ms = walk_ms / steps / n_tiles
+    achieved = per_launch / (avg_ms / 1e3) / 1e9
+    # DRAM bytes per launch from the committed ncu capture (None if the source changed since)
+    traffic = ncu_traffic(workload, kernel_name.split("<")[0])
+    peak, peak_kind = peaks()
+    # the counts are already their minimum: the lower-bound fraction is the same
+    return {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+            "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+            "traffic": traffic,
+            "traffic_gbs": None if traffic is None else traffic / (avg_ms / 1e3) / 1e9,
+            "algorithmic_bytes_per_launch": per_launch, "algorithmic_bytes_lower_bound": per_launch,
+            "frac_of_lower_bound": achieved / peak, "avg_launch_ms": avg_ms}
+
+
+def approx_side_record(P, rp, ci, steps: int, warmup: int, rank: int, flush):
+    """SpeedPPR (eps = 0.5) on R-MAT-22 with the workload's 256 sources in
+    16-column tiles, once drawing walks and once reading them from the
+    SpeedPPR-Index (built outside the timed region): queries/s from CUDA
+    events around each step, L2 flushed before every step, and the dominant
+    kernel's roofline entry."""
+    import torch
+    import ppr_inputs as gen
+    _, _, k, kt = WORKLOADS["rmat22-approx"]
+    n = len(rp) - 1
+    src = gen.sources(n, k, seed=replica_seed(3, rank))
+    g = P.Graph(rp, ci)
+    out = torch.empty((k, n), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    rec = {"graph": f"R-MAT scale 22, edge factor 16", "n": n, "m": len(ci), "eps": EPS, "alpha": ALPHA,
+           "sources_per_step": k, "k_tile": kt, "steps": steps, "warmup": warmup}
+    for label, indexed in (("walks", False), ("index", True)):
+        opts = dict(eps=EPS, alpha=ALPHA, k_tile=kt)
+        t_build = None
+        if indexed:
+            t = time.perf_counter()
+            g.build_index(0x1DE5, ALPHA)
+            torch.cuda.synchronize()
+            t_build = time.perf_counter() - t
+            opts["flags"] = P.PPR_FLAG_INDEX
+        for _ in range(warmup):
+            flush.zero_()
+            g.query(src, P.PPR_APPROX, out_pi=out, **opts)
+        torch.cuda.synchronize()
+        ms, walk_ms, st = [], 0.0, None
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = g.query(src, P.PPR_APPROX, out_pi=out, **opts)[1]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            walk_ms += st[0]["ms_walk"]
+        workload = "rmat22-index" if indexed else "rmat22-approx"
+        rec[label] = {"workload": workload, "ms_per_step": sum(ms) / steps,
+                      "queries_per_s": k * steps / (sum(ms) / 1e3),
+                      "roofline": approx_roofline(st, steps, -(-k // kt), walk_ms, kt, indexed, workload)}
+        if t_build is not None:
+            rec[label]["index_build_s"] = t_build
+    g.close()
+    return rec
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -419,6 +496,7 @@ def run_gpu(args):
         src22 = gen.sources(len(rp22) - 1, 64, seed=2)
         side["rmat22_k64"] = hp_side_record(P, "rmat22-k64", rp22, ci22, src22, min(args.steps, 5), 2, rank, local,
                                             flush)
+        side["speedppr_rmat22"] = approx_side_record(P, rp22, ci22, 2, 1, rank, flush)
         del rp22, ci22
         rpc, cic = gen.chung_lu(10_000, 100_000, 2.2, seed=1)
         srcc = gen.sources(len(rpc) - 1, 10, seed=1)
@@ -438,35 +516,8 @@ def run_gpu(args):
 
     value = ws * k * args.steps / (total_ms / 1e3)
     n_tiles = -(-k // kt)  # one walk (or index) launch per tile of kt sources
-    if indexed:
-        # dominant kernel: the index reads; per walk one 4 B index entry and the
-        # two 32 B sectors of its endpoint's count and estimate
-        walks_total = sum(x["walks"] for x in st) * args.steps
-        per_launch = 68 * walks_total / args.steps / n_tiles
-        avg_sweep_ms = sweep_ms / args.steps / n_tiles
-        kernel_name = f"index_query_kernel<{kt}>"
-    elif approx:
-        # dominant kernel: the walks; algorithmic bytes = two 32 B sectors per move
-        steps_total = sum(x["walk_steps"] for x in st) * args.steps
-        walks_total = sum(x["walks"] for x in st) * args.steps
-        per_launch = 64 * (steps_total + walks_total) / args.steps / n_tiles
-        avg_sweep_ms = sweep_ms / args.steps / n_tiles
-        kernel_name = f"walk_kernel<{kt}>"
     if approx:
-        # the other kernels' counts are already their minimum
-        per_launch_min = per_launch
-        achieved = per_launch / (avg_sweep_ms / 1e3) / 1e9
-        achieved_min = per_launch_min / (avg_sweep_ms / 1e3) / 1e9
-        # DRAM bytes per launch from the committed ncu capture (None if the source changed since)
-        traffic = ncu_traffic(args.workload, kernel_name.split("<")[0])
-        peak, peak_kind = peaks()
-        roofline = {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
-                    "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                    "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
-                    "traffic": traffic,
-                    "traffic_gbs": None if traffic is None else traffic / (avg_sweep_ms / 1e3) / 1e9,
-                    "algorithmic_bytes_per_launch": per_launch, "algorithmic_bytes_lower_bound": per_launch_min,
-                    "frac_of_lower_bound": achieved_min / peak, "avg_launch_ms": avg_sweep_ms}
+        roofline = approx_roofline(st, args.steps, n_tiles, sweep_ms, kt, indexed, args.workload)
     else:
         # dominant kernel: the FP32 correction pass (the Q1.63 passes only certify)
         roofline = hp_roofline(n, m, kt, fp32_ms, fp32_launches, sweep_ms, sweep_launches, args.workload)

@@ -94,3 +94,21 @@ def test_serving_admission_halves_then_refuses():
     assert bench.admit_batch(32, 100, 0, per_source) == 0     # refused: not even one fits
     assert bench.admit_batch(32, 0, 150, per_source) == 1     # the held workspace is reused
     assert bench.admit_batch(3, 349, 0, per_source) == 1      # 3 does not fit, 3 // 2 does
+
+
+def test_approx_roofline_entry(monkeypatch):
+    """Walks: two 32 B sectors per move and per endpoint; index reads: 68 B
+    per walk; both per launch (one launch per tile) over the kernel's mean
+    event time."""
+    monkeypatch.setattr(bench, "ncu_traffic", lambda workload, kernel="sweep_kernel": None)
+    st = [{"walks": 1000, "walk_steps": 4000}, {"walks": 3000, "walk_steps": 12000}]
+    # two tiles, three steps, 6 ms of walk-kernel time in all: 1 ms per launch
+    r = bench.approx_roofline(st, 3, 2, 6.0, 16, False, "rmat22-approx")
+    assert r["kernel"] == "walk_kernel<16>"
+    assert r["algorithmic_bytes_per_launch"] == 64 * (16000 + 4000) / 2
+    assert r["avg_launch_ms"] == pytest.approx(1.0)
+    assert r["achieved"] == pytest.approx(64 * 20000 / 2 / 1e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / bench.peaks()[0])
+    ri = bench.approx_roofline(st, 3, 2, 6.0, 16, True, "rmat22-index")
+    assert ri["kernel"] == "index_query_kernel<16>"
+    assert ri["algorithmic_bytes_per_launch"] == 68 * 4000 / 2
