@@ -126,7 +126,7 @@ def fp32_pass_bytes_min(n: int, m: int, kt: int) -> int:
 
 TRAFFIC_FILES = {
     # kernel family: (committed ncu summary, sources the capture was taken on)
-    "sweep_kernel": ("sweep_kernel_traffic.json", ("sweep_kernel.cuh",)),
+    "sweep_kernel": ("sweep_kernel_traffic.json", ("sweep_kernel.cuh", "fixconv.cuh")),
     # the FP32 pass's launch (its L2 window, the order of its work list) is set in hp.cu
     "refine_pass_kernel": ("refine_pass_kernel_traffic.json",
                            ("refine_kernel.cuh", "f32_lanes.cuh", "sweep_kernel.cuh", "fixconv.cuh", "hp.cu")),
