@@ -105,6 +105,18 @@ __device__ __forceinline__ typename Raw<T, V>::type zero_raw() {
 __device__ __forceinline__ float bf_lo(unsigned w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
 
+// a0 += lo(w), a1 += hi(w) for two BF16 values packed in w, each widened
+// exactly and added with one rounding (round to nearest), like
+// a0 += bf_lo(w), a1 += bf_hi(w), but as one mixed-precision add per value
+// (add.f32.bf16) instead of a shift or mask followed by an FP32 add: the
+// widening had made the ALU pipe the busiest one of the BF16 pass
+__device__ __forceinline__ void add_bf2(float& a0, float& a1, unsigned w) {
+  asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+      "add.rn.f32.bf16 %0, lo, %0;\n\tadd.rn.f32.bf16 %1, hi, %1;\n\t}"
+      : "+f"(a0), "+f"(a1)
+      : "r"(w));
+}
+
 template <typename T, int V>
 __device__ __forceinline__ void add_raw(float (&acc)[V], const typename Raw<T, V>::type& t) {
   if constexpr (std::is_same<T, float>::value) {
@@ -113,12 +125,15 @@ __device__ __forceinline__ void add_raw(float (&acc)[V], const typename Raw<T, V
     else { acc[0] += t; }
   } else {
     if constexpr (V == 8) {
-      acc[0] += bf_lo(t.x); acc[1] += bf_hi(t.x); acc[2] += bf_lo(t.y); acc[3] += bf_hi(t.y);
-      acc[4] += bf_lo(t.z); acc[5] += bf_hi(t.z); acc[6] += bf_lo(t.w); acc[7] += bf_hi(t.w);
+      add_bf2(acc[0], acc[1], t.x);
+      add_bf2(acc[2], acc[3], t.y);
+      add_bf2(acc[4], acc[5], t.z);
+      add_bf2(acc[6], acc[7], t.w);
     } else if constexpr (V == 4) {
-      acc[0] += bf_lo(t.x); acc[1] += bf_hi(t.x); acc[2] += bf_lo(t.y); acc[3] += bf_hi(t.y);
+      add_bf2(acc[0], acc[1], t.x);
+      add_bf2(acc[2], acc[3], t.y);
     } else if constexpr (V == 2) {
-      acc[0] += bf_lo(t); acc[1] += bf_hi(t);
+      add_bf2(acc[0], acc[1], t);
     } else {
       acc[0] += bf_lo((unsigned)t);
     }
