@@ -273,7 +273,9 @@ ppr_status ppr_selftest_fixconv(int64_t count, uint64_t seed, int64_t* out_misma
  * calls of a k of the same power-of-two bucket: the tile width and switch
  * for calls with k_tile = 0 / switch_edges = -1, w for every HP call (the
  * stats report it).  out_pi: device k x n float64 scratch for the calibration answers.
- * Widths whose workspace does not fit are skipped.  Errors as ppr_sssp_query.
+ * Widths whose workspace does not fit are skipped.  Errors as ppr_sssp_query,
+ * and PPR_ERR_NOT_CONVERGED when no candidate certifies the calibration batch
+ * within max_sweeps (nothing is remembered then).
  */
 ppr_status ppr_autotune(ppr_graph* g, const int32_t* src, int32_t k, const ppr_query_opts* base, double* out_pi,
                         ppr_query_opts* best, double* best_ms, void* cuda_stream);

@@ -121,6 +121,12 @@ extern "C" ppr_status ppr_autotune(ppr_graph* g, const int32_t* src, int32_t k, 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s != PPR_OK) return s;
+  if (!std::isfinite(best_t)) {
+    // no width and switch answered the calibration batch within max_sweeps:
+    // nothing is kept, later calls use the defaults
+    set_error("autotune: no candidate setting certified the calibration batch");
+    return PPR_ERR_NOT_CONVERGED;
+  }
   *best = best_o;
   if (best_ms) *best_ms = std::isfinite(best_wt) ? best_wt : best_t;
   g->tuned_kt[b] = best_o.k_tile;
